@@ -1,0 +1,379 @@
+"""Pins for the CPU oracle: each check is independent of the oracle's own code
+(dense numpy products, brute force in Python, closed forms, invariants, the
+paper's printed numbers), chosen so that a dropped term, a wrong index or a
+transposed operand in the oracle fails at least one of them.
+"""
+from __future__ import annotations
+
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from workloads.csc import CSC, from_coo, transpose, shuffle_within_columns, column_slice
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rand_csc(m, n, density, seed, *, vals="normal", index_dtype=np.int32, shuffle=True):
+    rng = np.random.default_rng(seed)
+    mask = rng.random((m, n)) < density
+    r, c = np.nonzero(mask)
+    if vals == "normal":
+        v = rng.standard_normal(r.size)
+    elif vals == "int":
+        v = rng.integers(-5, 6, r.size).astype(np.int64)
+    elif vals == "ones":
+        v = np.ones(r.size, dtype=np.int64)
+    else:
+        raise ValueError(vals)
+    a = from_coo(m, n, r, c, v, dup="error", index_dtype=index_dtype)
+    return shuffle_within_columns(a, seed + 7) if shuffle else a
+
+
+def dense_structure(A: CSC):
+    d = np.zeros((A.nrows, A.ncols), dtype=np.int64)
+    cols = np.repeat(np.arange(A.ncols), A.col_counts())
+    d[A.rowidx.astype(np.int64), cols] = 1
+    return d
+
+
+def read_golden_triples(path):
+    sections, cur = {}, None
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("["):
+            cur = line.strip("[]")
+            sections[cur] = []
+            continue
+        sections[cur].append([int(x) for x in line.split()])
+    return sections
+
+
+# --------------------------------------------------------------------------- c1
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("shape", [(7, 5, 6), (13, 17, 11), (32, 24, 40), (1, 9, 3)])
+def test_product_matches_dense_fp64(seed, shape):
+    m, k, n = shape
+    A = rand_csc(m, k, 0.3, seed)
+    B = rand_csc(k, n, 0.3, seed + 100)
+    C = oracle.spgemm(A, B)
+    Cd = A.to_dense().astype(np.float64) @ B.to_dense().astype(np.float64)
+    got = np.zeros((m, n))
+    cols = np.repeat(np.arange(n), C.col_counts())
+    got[C.rowidx, cols] = C.vals
+    np.testing.assert_allclose(got, Cd, rtol=1e-13, atol=1e-13)
+    # structure: exactly the entries reached by some product (boolean product)
+    S = (dense_structure(A) @ dense_structure(B)) > 0
+    sgot = np.zeros((m, n), dtype=bool)
+    sgot[C.rowidx, cols] = True
+    assert np.array_equal(S, sgot)
+    # rows sorted inside each column
+    for j in range(n):
+        seg = C.rowidx[C.colptr[j]:C.colptr[j + 1]]
+        assert np.all(np.diff(seg) > 0)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_product_matches_dense_int64(seed):
+    A = rand_csc(20, 15, 0.35, seed, vals="int")
+    B = rand_csc(15, 18, 0.35, seed + 50, vals="int")
+    C = oracle.spgemm(A, B)
+    assert C.vals.dtype == np.int64
+    Cd = A.to_dense().astype(np.int64) @ B.to_dense().astype(np.int64)
+    got = np.zeros_like(Cd)
+    cols = np.repeat(np.arange(C.ncols), C.col_counts())
+    got[C.rowidx, cols] = C.vals
+    assert np.array_equal(got, Cd)
+
+
+def test_zero_sums_are_kept_structurally():
+    # A(:,0) = [1, 1], A(:,1) = [1, -1]; B(:,0) = [1, 1]^T -> C(:,0) = [2, 0]
+    A = from_coo(2, 2, [0, 1, 0, 1], [0, 0, 1, 1], [1.0, 1.0, 1.0, -1.0])
+    B = from_coo(2, 1, [0, 1], [0, 0], [1.0, 1.0])
+    C = oracle.spgemm(A, B)
+    assert C.nnz == 2
+    assert list(C.rowidx) == [0, 1]
+    assert list(C.vals) == [2.0, 0.0]
+
+
+def test_int64_wraps_like_twos_complement():
+    big = (1 << 62) + 12345
+    A = from_coo(1, 3, [0, 0, 0], [0, 1, 2], np.array([big, big, -7], dtype=np.int64))
+    B = from_coo(3, 1, [0, 1, 2], [0, 0, 0], np.array([3, 5, 1 << 61], dtype=np.int64))
+    C = oracle.spgemm(A, B)
+    exact = big * 3 + big * 5 + (-7) * (1 << 61)
+    wrapped = (exact + (1 << 63)) % (1 << 64) - (1 << 63)
+    assert int(C.vals[0]) == wrapped
+
+
+def test_identity_is_neutral():
+    A = rand_csc(30, 20, 0.2, 3)
+    I_k = from_coo(20, 20, np.arange(20), np.arange(20), np.ones(20))
+    I_m = from_coo(30, 30, np.arange(30), np.arange(30), np.ones(30))
+    for C in (oracle.spgemm(A, I_k), oracle.spgemm(I_m, A)):
+        ref = oracle.canonical(A)
+        assert np.array_equal(C.colptr, ref.colptr)
+        assert np.array_equal(C.rowidx, ref.rowidx)
+        assert np.array_equal(C.vals, ref.vals.astype(np.float64))
+
+
+def test_path_counting_brute_force():
+    """Ones semiring: C(i,j) = #{k : A(i,k) != 0 and A(k,j) != 0}."""
+    A = rand_csc(14, 14, 0.25, 11, vals="ones")
+    C = oracle.spgemm(A, A)
+    S = dense_structure(A)
+    for j in range(14):
+        got = dict(zip(C.rowidx[C.colptr[j]:C.colptr[j + 1]].tolist(),
+                       C.vals[C.colptr[j]:C.colptr[j + 1]].tolist()))
+        for i in range(14):
+            paths = sum(1 for k in range(14) if S[i, k] and S[k, j])
+            assert got.get(i, 0) == paths
+            assert (i in got) == (paths > 0)
+
+
+def test_golden_worked_example():
+    g = read_golden_triples(os.path.join(GOLDEN, "worked_3x3.txt"))
+    def mk(rows):
+        r, c, v = zip(*rows)
+        return from_coo(3, 3, r, c, np.array(v, dtype=np.int64))
+    A, B, Cref = mk(g["A"]), mk(g["B"]), mk(g["C"])
+    C = oracle.spgemm(A, B)
+    assert np.array_equal(C.colptr, Cref.colptr.astype(np.int64))
+    assert np.array_equal(C.rowidx, Cref.rowidx.astype(np.int64))
+    assert np.array_equal(C.vals, Cref.vals)
+
+
+# ----------------------------------------------------------------- flops / c2/c3
+
+def test_flops_brute_force_and_cf():
+    A = rand_csc(25, 30, 0.2, 5)
+    B = rand_csc(30, 22, 0.2, 6)
+    f = oracle.flops_per_column(A, B)
+    SA, SB = dense_structure(A), dense_structure(B)
+    brute = np.array([sum(SA[:, k].sum() for k in range(30) if SB[k, j]) for j in range(22)])
+    assert np.array_equal(f, brute)
+    nnzc = oracle.symbolic(A, B)
+    assert np.all(nnzc <= f)          # cf >= 1 per column (Sec. II-A)
+    assert f.sum() >= nnzc.sum() > 0
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 7])
+def test_eq1_inequalities_and_stage_merge(s):
+    """Eq. (1): flops >= sum_t nnz(D_t) >= nnz(C); merging the stage products
+    gives the unsplit product."""
+    A = rand_csc(40, 35, 0.15, 21 + s)
+    B = rand_csc(35, 30, 0.15, 31 + s)
+    F = int(oracle.flops_per_column(A, B).sum())
+    C = oracle.spgemm(A, B)
+    parts = [oracle.spgemm(A, B, krange=kr) for kr in oracle.stage_ranges(A.ncols, s)]
+    U = sum(p.nnz for p in parts)
+    assert F >= U >= C.nnz
+    assert sum(int(oracle.flops_per_column(A, B, kr).sum())
+               for kr in oracle.stage_ranges(A.ncols, s)) == F
+    M = oracle.merge(parts)
+    assert np.array_equal(M.colptr, C.colptr) and np.array_equal(M.rowidx, C.rowidx)
+    np.testing.assert_allclose(M.vals, C.vals, rtol=1e-12, atol=1e-14)
+    # stage ranges tile [0, k) contiguously
+    kr = oracle.stage_ranges(A.ncols, s)
+    assert kr[0][0] == 0 and kr[-1][1] == A.ncols
+    assert all(kr[i][1] == kr[i + 1][0] for i in range(s - 1))
+
+
+def test_merge_matches_dense_sum_int():
+    parts = [rand_csc(12, 9, 0.3, 70 + t, vals="int") for t in range(3)]
+    M = oracle.merge(parts)
+    ref = sum(p.to_dense().astype(np.int64) for p in parts)
+    got = np.zeros_like(ref)
+    cols = np.repeat(np.arange(9), M.col_counts())
+    got[M.rowidx, cols] = M.vals
+    assert np.array_equal(got, ref)
+    S = sum(dense_structure(p) for p in parts) > 0
+    assert M.nnz == int(S.sum())
+
+
+def test_symbolic_equals_numeric_nnz_and_boolean_popcount():
+    A = rand_csc(50, 45, 0.08, 41)
+    B = rand_csc(45, 60, 0.08, 42)
+    cnt = oracle.symbolic(A, B)
+    C = oracle.spgemm(A, B)
+    assert np.array_equal(cnt, C.col_counts())
+    S = (dense_structure(A) @ dense_structure(B)) > 0
+    assert np.array_equal(cnt, S.sum(axis=0))
+
+
+def test_column_ranges_concatenate_to_whole():
+    """ColConcat of batches equals the unbatched product (Algorithm 4)."""
+    A = rand_csc(30, 30, 0.15, 51)
+    C = oracle.spgemm(A, A)
+    pieces = [oracle.spgemm(A, A, cols=(c0, c1)) for c0, c1 in [(0, 7), (7, 8), (8, 8), (8, 30)]]
+    rows = np.concatenate([p.rowidx for p in pieces])
+    vals = np.concatenate([p.vals for p in pieces])
+    counts = np.concatenate([p.col_counts() for p in pieces])
+    assert np.array_equal(counts, C.col_counts())
+    assert np.array_equal(rows, C.rowidx) and np.array_equal(vals, C.vals)
+
+
+def test_row_order_invariance():
+    """Sort-free inputs (Sec. IV-D): shuffling rows inside input columns
+    changes nothing after the canonical sort."""
+    A = rand_csc(35, 28, 0.2, 61, vals="int", shuffle=False)
+    B = rand_csc(28, 33, 0.2, 62, vals="int", shuffle=False)
+    C0 = oracle.spgemm(A, B)
+    C1 = oracle.spgemm(shuffle_within_columns(A, 1), shuffle_within_columns(B, 2))
+    assert np.array_equal(C0.rowidx, C1.rowidx) and np.array_equal(C0.vals, C1.vals)
+
+
+def test_semiring_invariants():
+    A = rand_csc(26, 19, 0.2, 71)
+    B = rand_csc(19, 23, 0.2, 72)
+    C = oracle.spgemm(A, B)
+    ones = np.ones(23)
+    Cd = np.zeros((26, 23))
+    cols = np.repeat(np.arange(23), C.col_counts())
+    Cd[C.rowidx, cols] = C.vals
+    lhs = Cd @ ones
+    rhs = A.to_dense() @ (B.to_dense() @ ones)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-12, atol=1e-12)
+    # (AB)^T = B^T A^T
+    Ct = oracle.spgemm(transpose(B), transpose(A))
+    CT = transpose(CSC(C.nrows, C.ncols, C.colptr, C.rowidx, C.vals))
+    assert np.array_equal(Ct.colptr, CT.colptr.astype(np.int64))
+    assert np.array_equal(Ct.rowidx, CT.rowidx.astype(np.int64))
+    np.testing.assert_allclose(Ct.vals, CT.vals, rtol=1e-13, atol=1e-13)
+
+
+def test_absterm_bounds_value():
+    A = rand_csc(20, 20, 0.3, 81)
+    C, ab = oracle.spgemm(A, A, with_absterm=True)
+    assert np.all(np.abs(C.vals) <= ab * (1 + 1e-12))
+    Ad = np.abs(A.to_dense())
+    Sd = Ad @ Ad
+    cols = np.repeat(np.arange(20), C.col_counts())
+    np.testing.assert_allclose(ab, Sd[C.rowidx, cols], rtol=1e-13)
+
+
+# ----------------------------------------------------------------------- c3 plan
+
+def test_plan_batches_greedy_is_minimal_and_valid():
+    rng = np.random.default_rng(91)
+    for trial in range(200):
+        n = int(rng.integers(1, 9))
+        w = rng.integers(0, 10, n)
+        cap = int(rng.integers(1, 20))
+        begin = oracle.plan_batches(w, cap)
+        if w.max() > cap:
+            assert begin is None
+            continue
+        b = len(begin) - 1
+        assert begin[0] == 0 and begin[-1] == n
+        for t in range(b):
+            seg = w[begin[t]:begin[t + 1]]
+            assert seg.sum() <= cap and begin[t + 1] > begin[t]
+            if t + 1 < b:  # greedy: the next column would not have fit
+                assert seg.sum() + w[begin[t + 1]] > cap
+        # brute force: no contiguous partition uses fewer ranges
+        best = n + 1
+        for mask in range(1 << (n - 1)):
+            cuts = [0] + [i + 1 for i in range(n - 1) if mask >> i & 1] + [n]
+            if all(w[cuts[i]:cuts[i + 1]].sum() <= cap for i in range(len(cuts) - 1)):
+                best = min(best, len(cuts) - 1)
+        assert b == best
+        assert b >= -(-int(w.sum()) // cap)   # Eq. (2)-style lower bound
+
+
+def test_eq2_bound_and_paper_memory_example():
+    vals = {}
+    for line in open(os.path.join(GOLDEN, "paper_memory_example.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    r = int(vals["r"])
+    assert oracle.mem_bytes(r, [int(vals["nnz_c"])]) == int(vals["final_output_bytes"])
+    assert oracle.mem_bytes(r, [int(vals["flops"])]) == int(vals["worst_case_bytes"])
+    # Eq. (2) with the paper's printed sizes: 2208 TB over 1.09 PB minus inputs
+    b = oracle.batch_lower_bound(int(vals["worst_case_bytes"]), int(vals["aggregate_memory_bytes"]),
+                                 r, int(vals["nnz_a"]), int(vals["nnz_a"]))
+    den = vals["aggregate_memory_bytes"] - r * 2 * vals["nnz_a"]
+    assert b == int(np.ceil(vals["worst_case_bytes"] / den)) == 3
+    assert oracle.batch_lower_bound(10, 5, 1, 3, 3) == -1
+    assert oracle.batch_lower_bound(0, 100, 1, 1, 1) == 1
+    assert oracle.batch_lower_bound(101, 102, 1, 1, 0) == 1
+    assert oracle.batch_lower_bound(102, 102, 1, 1, 0) == 2
+
+
+# ----------------------------------------------------------------------- c7
+
+def _loss(A, B, G):
+    C = oracle.spgemm(A, B)
+    Gc = oracle.canonical(G)
+    assert np.array_equal(C.rowidx, Gc.rowidx)
+    return float(np.dot(C.vals, Gc.vals))
+
+
+def test_backward_finite_differences_exact_for_bilinear_loss():
+    A, B = W.config5(m=64, k=64, n=64, value_dtype=np.float64)
+    C = oracle.spgemm(A, B)
+    G = W.values_on_pattern(C, 5, dist="normal", value_dtype=np.float64)
+    G = shuffle_within_columns(G, 3)
+    dA, dB = oracle.backward(A, B, G)
+    h = 1e-3
+    rng = np.random.default_rng(0)
+    for q in rng.choice(A.nnz, 40, replace=False):
+        Ap = CSC(A.nrows, A.ncols, A.colptr, A.rowidx, A.vals.copy()); Ap.vals[q] += h
+        Am = CSC(A.nrows, A.ncols, A.colptr, A.rowidx, A.vals.copy()); Am.vals[q] -= h
+        fd = (_loss(Ap, B, G) - _loss(Am, B, G)) / (2 * h)
+        assert abs(fd - dA[q]) <= 1e-9 * max(1.0, abs(dA[q]))
+    for p in rng.choice(B.nnz, 40, replace=False):
+        Bp = CSC(B.nrows, B.ncols, B.colptr, B.rowidx, B.vals.copy()); Bp.vals[p] += h
+        Bm = CSC(B.nrows, B.ncols, B.colptr, B.rowidx, B.vals.copy()); Bm.vals[p] -= h
+        fd = (_loss(A, Bp, G) - _loss(A, Bm, G)) / (2 * h)
+        assert abs(fd - dB[p]) <= 1e-9 * max(1.0, abs(dB[p]))
+
+
+def test_backward_matches_dense_masked_products():
+    A = rand_csc(18, 14, 0.3, 101)
+    B = rand_csc(14, 16, 0.3, 102)
+    C = oracle.spgemm(A, B)
+    G = W.values_on_pattern(C, 9, dist="normal", value_dtype=np.float64)
+    dA, dB = oracle.backward(A, B, G)
+    Gd = G.to_dense()
+    dAd = Gd @ B.to_dense().T
+    dBd = A.to_dense().T @ Gd
+    colsA = np.repeat(np.arange(A.ncols), A.col_counts())
+    colsB = np.repeat(np.arange(B.ncols), B.col_counts())
+    np.testing.assert_allclose(dA, dAd[A.rowidx, colsA], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(dB, dBd[B.rowidx, colsB], rtol=1e-12, atol=1e-12)
+
+
+# ----------------------------------------------------------------- generators
+
+def test_generators_shapes_and_recipes():
+    A1 = W.config1(n=256)
+    A1.validate()
+    assert np.all(A1.col_counts() == 8)
+    assert A1.vals.dtype == np.float64 and A1.rowidx.dtype == np.int32
+    A2 = W.config2(scale=10, edge_factor=16)
+    A2.validate()
+    d2 = A2.to_dense()
+    assert np.allclose(d2, d2.T)          # X + X^T is symmetric
+    A3 = W.config3(n=5000)
+    A3.validate()
+    d3 = A3.to_dense()
+    assert np.array_equal(d3, d3.T)
+    assert A3.rowidx.dtype == np.int64
+    assert 0.3 <= A3.vals.min() and A3.vals.max() <= 1.0
+    probs = W.config4(count=6, nmax=3000)
+    for P in probs:
+        P.validate()
+        assert np.all(P.vals == 1)
+    A5, B5 = W.config5(m=300, k=300, n=150)
+    assert np.all(A5.col_counts() == 16) and np.all(B5.col_counts() == 8)
+    # determinism
+    assert np.array_equal(W.config1(n=256).rowidx, A1.rowidx)
