@@ -1,0 +1,301 @@
+/*
+ * spgemm.h -- C ABI of the GB300 (sm_103a) memory-constrained SpGEMM library.
+ *
+ * The library computes C = A * B for sparse matrices in compressed sparse
+ * column (CSC) form over the plus-times semiring, with int32 or int64 indices
+ * and float64, float32 or int64 values. It restates, for one GPU, the local
+ * hot path of Hussain, Selvitopi, Buluc and Azad, "Communication-Avoiding and
+ * Memory-Constrained Sparse Matrix-Matrix Multiplication at Extreme Scale":
+ *
+ *   - the symbolic step that counts nonzeros per output column and chooses the
+ *     number of column batches b for a memory budget (Algorithm 3, Eq. (2));
+ *   - the sort-free hash-accumulator Gustavson multiply (Sec. II-C formula,
+ *     Sec. IV-D "sort-free local SpGEMM");
+ *   - the sort-free hash merge of partial products when the inner dimension is
+ *     split into stages (Algorithm 1's stages and merge, Sec. IV-D);
+ *   - the batch loop that hands each finished column batch of C to the host
+ *     (Algorithm 4).
+ *
+ * Conventions for every call:
+ *   - Every function returns an spgemm_status; no exception or abort crosses
+ *     the ABI. spgemm_last_error() returns a message for the calling thread's
+ *     last failure.
+ *   - Matrix pointers inside spgemm_csc are DEVICE pointers unless a call says
+ *     otherwise. The caller owns them; the library never frees them.
+ *   - Rows inside an input column may be stored in any order. An input (row,
+ *     col) pair that appears twice behaves as if its values were summed.
+ *   - Output columns are NOT sorted by row unless a call says so (the paper
+ *     keeps intermediate results unsorted, Sec. IV-D).
+ *   - Structural nonzeros of C are all (i, j) reached by at least one product
+ *     A(i,k) B(k,j); sums that cancel to zero are still stored.
+ *   - float32 products are accumulated in float32, float64 in float64, int64
+ *     with two's-complement wrap-around. Floating-point summation order is
+ *     unspecified (hash-table atomics), so results may differ in the last bits
+ *     between runs.
+ *   - Calls enqueue work on the given stream and return without waiting,
+ *     except where a call documents a host synchronisation.
+ *   - A plan is not thread-safe; use one plan per host thread.
+ *   - There is no CPU fallback: without a usable sm_103a device every compute
+ *     call returns SPGEMM_ERR_CUDA.
+ */
+#ifndef SPGEMM_GB300_H
+#define SPGEMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPGEMM_OK = 0,
+    SPGEMM_ERR_INVALID = 1,        /* bad argument, shape or type mismatch, corrupt CSC */
+    SPGEMM_ERR_OOM = 2,            /* device or pinned-host allocation failed */
+    SPGEMM_ERR_BUDGET = 3,         /* budget below A + B + workspace, or one column alone exceeds a batch */
+    SPGEMM_ERR_OVERFLOW = 4,       /* a hash table probe exceeded its bound (internal error guard) */
+    SPGEMM_ERR_INDEX_OVERFLOW = 5, /* an output offset does not fit the requested index type */
+    SPGEMM_ERR_CUDA = 6,           /* a CUDA runtime call failed (message has the CUDA error) */
+    SPGEMM_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up */
+    SPGEMM_ERR_SINK = 8,           /* the batch sink callback returned non-zero */
+    SPGEMM_ERR_STATE = 9           /* call out of order (e.g. numeric before symbolic) */
+} spgemm_status;
+
+typedef enum { SPGEMM_I32 = 0, SPGEMM_I64 = 1 } spgemm_index_t;
+typedef enum { SPGEMM_F64 = 0, SPGEMM_F32 = 1, SPGEMM_INT64 = 2 } spgemm_value_t;
+
+/*
+ * A CSC matrix: colptr[ncols+1] (type ptr_type), rowidx[nnz] and vals[nnz]
+ * (types idx_type and val_type). For inputs ptr_type must equal idx_type.
+ * For outputs ptr_type may be SPGEMM_I64 while idx_type is SPGEMM_I32.
+ * Row indices must be < 2^31 - 1 (the hash tables hold 32-bit keys).
+ */
+typedef struct {
+    int64_t nrows;
+    int64_t ncols;
+    int64_t nnz;
+    void *colptr;
+    void *rowidx;
+    void *vals;
+    spgemm_index_t ptr_type;
+    spgemm_index_t idx_type;
+    spgemm_value_t val_type;
+} spgemm_csc;
+
+/*
+ * Tuning knobs. Zero in any field means "library default". The autotuner in
+ * the Python package fills these from timed trials.
+ *   hash_max_cap   largest column (distinct rows) kept in a shared-memory hash
+ *                  table; larger columns use the dense row-panel accumulator.
+ *                  Powers of two from 256 to 8192.
+ *   panel_rows     rows per dense row panel (2^13, 2^14 or 2^15).
+ *   short_seg      A-column segments up to this length are walked by one thread;
+ *                  longer ones by a whole warp (1..64).
+ *   huge_seg       segments longer than this are walked by the whole CTA.
+ *   block_tier_threads  threads per CTA of the hash tiers (128..1024).
+ */
+typedef struct {
+    int hash_max_cap;
+    int panel_rows;
+    int short_seg;
+    int huge_seg;
+    int block_tier_threads;
+    int reserved[3];
+} spgemm_tuning;
+
+typedef struct {
+    size_t budget_bytes;     /* device memory for A, B, workspace and batch outputs;
+                                0 = 80% of the free device memory at plan time */
+    int kstages;             /* s >= 1: split the inner dimension into s contiguous stages
+                                (A by columns, B by rows) and hash-merge the partials */
+    int ring_depth;          /* device output buffers kept in flight by spgemm_run_batched (>= 1; 0 = 2) */
+    size_t host_slot_bytes;  /* pinned host slot size for spgemm_run_batched (0 = 256 MiB) */
+    int host_slots;          /* pinned host slots (>= 2; 0 = 3) */
+    int sort_output;         /* 1: sort rows inside each output column (the paper's final output);
+                                0: unsorted */
+    const spgemm_tuning *tuning; /* NULL = defaults */
+} spgemm_opts;
+
+typedef struct spgemm_plan_s spgemm_plan;
+
+/* Summary filled by spgemm_plan_query after spgemm_symbolic. */
+typedef struct {
+    int64_t flops;            /* sum_j f_j: multiplications (Sec. II-A) */
+    int64_t nnz_c;            /* nnz(C) */
+    int64_t unmerged_nnz;     /* sum_t nnz(D_t) over the s stages (= nnz_c when s = 1) */
+    int64_t nbatches;         /* b */
+    int64_t max_batch_nnz;    /* largest nnz(C) of one batch */
+    int64_t max_batch_cols;
+    int64_t bytes_per_nnz;    /* r = index bytes + value bytes */
+    int64_t batch_cap_bytes;  /* bytes one batch may occupy on the device */
+    int64_t heavy_columns;    /* columns handled by the dense row-panel accumulator */
+} spgemm_plan_info;
+
+/* Thread-local message of the last failing call (never NULL). */
+const char *spgemm_last_error(void);
+
+/* Library version string. */
+const char *spgemm_version(void);
+
+/*
+ * spgemm_plan_create -- validate A and B and set up a plan for C = A * B.
+ * Checks A.ncols == B.nrows, equal index and value types, nnz == colptr[ncols]
+ * (one device read) and, when validate != 0, monotone colptr and rows in range
+ * (a device check, one synchronisation). Allocates plan workspace with
+ * cudaMalloc. A and B must stay valid and unchanged for the plan's lifetime.
+ * Errors: SPGEMM_ERR_INVALID, SPGEMM_ERR_OOM, SPGEMM_ERR_CUDA.
+ */
+spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B,
+                                 const spgemm_opts *opts, int validate,
+                                 cudaStream_t stream, spgemm_plan **out);
+
+/* Release a plan and all workspace it owns. NULL is accepted. */
+spgemm_status spgemm_plan_destroy(spgemm_plan *plan);
+
+/*
+ * spgemm_symbolic -- the symbolic step (Algorithm 3 on one device):
+ * flops per column (Sec. II-A), exact nnz per output column by hash /
+ * bitmap insertion (LocalSymbolic), with s > 1 also the per-stage counts
+ * nnz(D_t(:, j)) whose sum is the unmerged memory of Eq. (1), and the batch
+ * plan: the smallest number of contiguous column ranges whose outputs fit the
+ * budget (Eq. (2), Sec. V-C). Synchronises the stream once (to read totals).
+ * Errors: SPGEMM_ERR_BUDGET (inputs alone exceed the budget, or one column's
+ * output exceeds a batch), SPGEMM_ERR_CUDA, SPGEMM_ERR_OOM.
+ */
+spgemm_status spgemm_symbolic(spgemm_plan *plan, cudaStream_t stream);
+
+/* Plan summary (host struct). Errors: SPGEMM_ERR_STATE before symbolic. */
+spgemm_status spgemm_plan_query(const spgemm_plan *plan, spgemm_plan_info *info);
+
+/* Column range [col_begin, col_end) and nnz of batch t (host values). */
+spgemm_status spgemm_plan_batch(const spgemm_plan *plan, int64_t t, int64_t *col_begin,
+                                int64_t *col_end, int64_t *nnz);
+
+/*
+ * Copy the per-column output counts nnz(C(:, j)) (int64, B.ncols entries) to
+ * the device buffer counts_out, enqueued on stream.
+ */
+spgemm_status spgemm_plan_column_counts(const spgemm_plan *plan, int64_t *counts_out,
+                                        cudaStream_t stream);
+
+/*
+ * Write the colptr of the whole product C (ncols+1 entries of type ptr_type,
+ * device buffer) on stream. Errors: SPGEMM_ERR_STATE, SPGEMM_ERR_INDEX_OVERFLOW
+ * (nnz(C) does not fit a 32-bit colptr).
+ */
+spgemm_status spgemm_plan_colptr(const spgemm_plan *plan, void *colptr_out,
+                                 spgemm_index_t ptr_type, cudaStream_t stream);
+
+/*
+ * Synchronise the stream and report the plan's device error flags: returns
+ * SPGEMM_ERR_OVERFLOW if a kernel found a hash probe sequence longer than its
+ * table or a column whose numeric nnz differed from its symbolic count
+ * (internal consistency guards; neither happens on valid input).
+ */
+spgemm_status spgemm_plan_check(const spgemm_plan *plan, cudaStream_t stream);
+
+/*
+ * spgemm_numeric -- compute batch t of C (columns [col_begin, col_end) of the
+ * plan) into caller-allocated device buffers: C_out->colptr (ncols+1 entries,
+ * offsets relative to the batch), rowidx and vals (nnz entries each), with
+ * nrows = A.nrows, ncols and nnz as spgemm_plan_batch reports. Columns are
+ * unsorted unless opts.sort_output. With s > 1 stages the stage products
+ * D_t are formed in plan workspace and hash-merged (Algorithm 1's merge).
+ * Errors: SPGEMM_ERR_STATE, SPGEMM_ERR_INVALID (shape/type of C_out),
+ * SPGEMM_ERR_INDEX_OVERFLOW (nnz does not fit a 32-bit colptr), SPGEMM_ERR_CUDA,
+ * SPGEMM_ERR_OVERFLOW (internal hash-probe guard tripped).
+ */
+spgemm_status spgemm_numeric(spgemm_plan *plan, int64_t t, spgemm_csc *C_out,
+                             cudaStream_t stream);
+
+/*
+ * spgemm_merge -- sort-free hash merge (Sec. IV-D): out(:, j) = sum over parts
+ * of parts[i](:, j), adding values of equal rows. All parts share shape and
+ * types. Two calls: with out->rowidx == NULL the call fills out->colptr
+ * (device, ncols+1, type out->ptr_type) and sets out->nnz, synchronising the
+ * stream once; the second call (rowidx and vals allocated with out->nnz
+ * entries, colptr unchanged) fills them. Unsorted output.
+ * Errors: SPGEMM_ERR_INVALID, SPGEMM_ERR_CUDA, SPGEMM_ERR_OOM, SPGEMM_ERR_INDEX_OVERFLOW.
+ */
+spgemm_status spgemm_merge(const spgemm_csc *parts, int nparts, spgemm_csc *out,
+                           cudaStream_t stream);
+
+/*
+ * Sink for spgemm_run_batched. Called on the calling host thread once per
+ * finished piece of C: columns [col_begin, col_end) of C, a CSC whose arrays
+ * are PINNED HOST memory owned by the library and valid only during the call
+ * (colptr is int64 and relative to the piece). A batch arrives as one or more
+ * pieces, in column order. Return 0 to continue, non-zero to stop (the run
+ * then drains in-flight copies and returns SPGEMM_ERR_SINK).
+ */
+typedef int (*spgemm_sink_fn)(void *ctx, int64_t batch, int64_t col_begin, int64_t col_end,
+                              const spgemm_csc *piece);
+
+/*
+ * spgemm_run_batched -- the memory-constrained batch loop (Algorithm 4): for
+ * every batch t = 0..b-1, compute C[t] on `compute` into one of ring_depth
+ * device buffers, then copy it on `copy` into pinned host slots and hand it to
+ * the sink, overlapping the copy of batch t with the multiply of batch t+1.
+ * Requires spgemm_symbolic first. Returns after the last sink call.
+ * Errors: SPGEMM_ERR_SINK, SPGEMM_ERR_OOM, SPGEMM_ERR_CUDA, SPGEMM_ERR_STATE.
+ */
+spgemm_status spgemm_run_batched(spgemm_plan *plan, spgemm_sink_fn sink, void *ctx,
+                                 cudaStream_t compute, cudaStream_t copy);
+
+/*
+ * spgemm_backward -- gradients of loss = sum over pattern(C) of C(i,j) G(i,j)
+ * with respect to the stored values of A and B (not in the paper; follows
+ * from the Sec. II-C product): dA(i,k) = sum_j G(i,j) B(k,j) on pattern(A),
+ * dB(k,j) = sum_i A(i,k) G(i,j) on pattern(B). G is a device CSC with C's
+ * shape and pattern (any row order inside columns), same value type as A.
+ * dA_vals / dB_vals are device arrays of nnz(A) / nnz(B) values in A's / B's
+ * storage order, overwritten. Floating-point values only. Works on plans with
+ * s = 1; needs no symbolic step (G carries the pattern).
+ * Errors: SPGEMM_ERR_INVALID, SPGEMM_ERR_CUDA, SPGEMM_ERR_OVERFLOW.
+ */
+spgemm_status spgemm_backward(spgemm_plan *plan, const spgemm_csc *G, void *dA_vals,
+                              void *dB_vals, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Many independent products C_i = A_i * B_i of uneven sizes in one pass.
+ * ------------------------------------------------------------------------- */
+typedef struct spgemm_multi_s spgemm_multi;
+
+/*
+ * spgemm_multi_create -- plan nprob products (all with the same index and
+ * value types). The host arrays As and Bs (nprob entries each) are copied;
+ * their device buffers must stay valid. The output is one arena: the
+ * concatenation of the C_i column by column (C_i's columns follow C_{i-1}'s;
+ * rows stay local to each problem), with an int64 colptr over all
+ * sum_i B_i.ncols columns. The arena is sized from the flop count
+ * (nnz(C_i) <= flops_i), so the whole pipeline needs no host synchronisation
+ * and can be captured in a CUDA graph. Errors: SPGEMM_ERR_INVALID, SPGEMM_ERR_OOM,
+ * SPGEMM_ERR_CUDA.
+ */
+spgemm_status spgemm_multi_create(int nprob, const spgemm_csc *As, const spgemm_csc *Bs,
+                                  const spgemm_opts *opts, cudaStream_t stream,
+                                  spgemm_multi **out);
+
+spgemm_status spgemm_multi_destroy(spgemm_multi *m);
+
+/*
+ * spgemm_multi_run -- flops, symbolic, scan and numeric for all problems,
+ * enqueued on stream without host synchronisation. With use_graph != 0 the
+ * sequence is captured once into a CUDA graph and replayed on later calls.
+ */
+spgemm_status spgemm_multi_run(spgemm_multi *m, int use_graph, cudaStream_t stream);
+
+/*
+ * Device pointers of the output arena (valid until destroy): colptr (int64,
+ * total_cols+1 entries, global offsets), rowidx (index type of the inputs),
+ * vals; plus total_cols and the arena capacity in entries. The product's nnz
+ * is colptr[total_cols] (read it after the stream completes).
+ */
+spgemm_status spgemm_multi_output(const spgemm_multi *m, int64_t **colptr, void **rowidx,
+                                  void **vals, int64_t *total_cols, int64_t *capacity);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPGEMM_GB300_H */

@@ -1,0 +1,37 @@
+"""GB300 (sm_103a) memory-constrained SpGEMM -- Python binding.
+
+Thin marshalling over the C ABI in include/spgemm.h: every step of the
+product (flop count, symbolic count, batch plan, hash / dense numeric, merge,
+backward) runs in the library's CUDA kernels. torch supplies device memory
+and streams. There is no CPU fallback: without the built library or a GPU,
+calls raise.
+
+Main entry points
+-----------------
+``Csc``                 device CSC matrix (torch tensors)
+``Plan``                symbolic step, batch plan, numeric per batch
+``spgemm(A, B)``        C = A*B (all batches concatenated)
+``merge(parts)``        sort-free hash merge of partial products
+``run_batched(...)``    batch loop streaming C to pinned host memory
+``SpGEMMFn``            autograd Function (masked-SpGEMM backward)
+``Multi``               many independent products in one pass (CUDA graph)
+"""
+from __future__ import annotations
+
+from ._capi import SpgemmError, load
+from .core import (
+    Csc,
+    Plan,
+    Tuning,
+    spgemm,
+    merge,
+    run_batched,
+    backward,
+    SpGEMMFn,
+    Multi,
+)
+
+__all__ = [
+    "SpgemmError", "load", "Csc", "Plan", "Tuning", "spgemm", "merge", "run_batched",
+    "backward", "SpGEMMFn", "Multi",
+]

@@ -1,0 +1,854 @@
+// Typed host driver of the kernels: symbolic step, batch plan, numeric step
+// (plain or k-split + hash merge), standalone merge, backward.
+#pragma once
+
+#include <algorithm>
+#include <array>
+#include <cstring>
+#include <vector>
+
+#include "kernels.cuh"
+#include "plan.h"
+#include "util.h"
+
+namespace spg {
+
+#define SPG_CK(call)                                                   \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);            \
+    } while (0)
+
+#define SPG_ST(...)                                                    \
+    do {                                                               \
+        spgemm_status s_ = (__VA_ARGS__);                              \
+        if (s_ != SPGEMM_OK) return s_;                                \
+    } while (0)
+
+inline int block_tier_threads(int T, const Tuning &tun) {
+    if (tun.block_threads) return tun.block_threads;
+    if (T <= 1024) return 128;
+    if (T <= 4096) return 256;
+    if (T <= 8192) return 512;
+    return 1024;
+}
+
+// Scratch shared by one symbolic / numeric pass.
+struct Ctx {
+    int nsm;
+    Tuning tun;
+    int *err;
+    int32_t *hist;       // 64 ints
+    int32_t *cursor;     // 64 ints
+    int32_t *h_small;    // pinned host, >= 64 ints
+    int P, Q;
+    int64_t Rs;
+};
+
+inline Ctx make_ctx(PlanState &ps) {
+    Ctx c;
+    c.nsm = ps.nsm; c.tun = ps.tun; c.err = ps.err.as<int>();
+    c.hist = ps.hist.as<int32_t>(); c.cursor = ps.cursor.as<int32_t>();
+    c.h_small = ps.h_small.as<int32_t>();
+    c.P = ps.P; c.Q = ps.Q; c.Rs = ps.Rs;
+    return c;
+}
+
+inline TierCommon common_of(const Ctx &c) {
+    TierCommon t{};
+    t.short_seg = c.tun.short_seg;
+    t.huge_seg = c.tun.huge_seg;
+    t.err = c.err;
+    t.hash_cap_max = c.tun.hash_cap_max;
+    t.P = c.P; t.log2R = c.tun.log2R; t.Rs = c.Rs; t.Q = c.Q;
+    return t;
+}
+
+template <class K> static void set_smem(K kern, int bytes) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// Output of a numeric pass.
+template <class I, class V> struct NumOut {
+    const int64_t *colptr;
+    int64_t out_base;
+    I *rows;
+    V *vals;
+};
+
+template <class I, class V> struct Engine : EngineBase {
+    using PD = ProbDev<I, V>;
+    using GA = GemmArgs<I, V>;
+    using PA = PartsArgs<I, V>;
+
+    // ---- one-time attributes ----------------------------------------------
+    static void attrs() {
+        static bool done = false;
+        if (done) return;
+        const int sv = (int)(sizeof(V) + 4);
+        const int mx = 220 * 1024;
+        set_smem(k_sym_block<SrcGemm<I, V>, 512>, mx);
+        set_smem(k_sym_block<SrcGemm<I, V>, 1024>, mx);
+        set_smem(k_sym_block<SrcGemm<I, V>, 2048>, mx);
+        set_smem(k_sym_block<SrcGemm<I, V>, 4096>, mx);
+        set_smem(k_sym_block<SrcGemm<I, V>, 8192>, mx);
+        set_smem(k_sym_block<SrcGemm<I, V>, 16384>, mx);
+        set_smem(k_sym_block<SrcParts<I, V>, 512>, mx);
+        set_smem(k_sym_block<SrcParts<I, V>, 1024>, mx);
+        set_smem(k_sym_block<SrcParts<I, V>, 2048>, mx);
+        set_smem(k_sym_block<SrcParts<I, V>, 4096>, mx);
+        set_smem(k_sym_block<SrcParts<I, V>, 8192>, mx);
+        set_smem(k_sym_block<SrcParts<I, V>, 16384>, mx);
+        set_smem(k_num_block<SrcGemm<I, V>, 512>, mx);
+        set_smem(k_num_block<SrcGemm<I, V>, 1024>, mx);
+        set_smem(k_num_block<SrcGemm<I, V>, 2048>, mx);
+        set_smem(k_num_block<SrcGemm<I, V>, 4096>, mx);
+        set_smem(k_num_block<SrcGemm<I, V>, 8192>, mx);
+        set_smem(k_num_block<SrcGemm<I, V>, 16384>, mx);
+        set_smem(k_num_block<SrcParts<I, V>, 512>, mx);
+        set_smem(k_num_block<SrcParts<I, V>, 1024>, mx);
+        set_smem(k_num_block<SrcParts<I, V>, 2048>, mx);
+        set_smem(k_num_block<SrcParts<I, V>, 4096>, mx);
+        set_smem(k_num_block<SrcParts<I, V>, 8192>, mx);
+        set_smem(k_num_block<SrcParts<I, V>, 16384>, mx);
+        set_smem(k_bwd_block<I, V, 512>, mx);
+        set_smem(k_bwd_block<I, V, 1024>, mx);
+        set_smem(k_bwd_block<I, V, 2048>, mx);
+        set_smem(k_bwd_block<I, V, 4096>, mx);
+        set_smem(k_bwd_block<I, V, 8192>, mx);
+        set_smem(k_bwd_block<I, V, 16384>, mx);
+        set_smem(k_sym_bitmap<SrcGemm<I, V>>, mx);
+        set_smem(k_sym_bitmap<SrcParts<I, V>>, mx);
+        set_smem(k_num_dense<SrcPanel<I, V>>, mx);
+        set_smem(k_num_dense<SrcPartsPanel<I, V>>, mx);
+        set_smem(k_bwd_dense<I, V>, mx);
+        (void)sv;
+        done = true;
+    }
+
+    // ---- tier launches -----------------------------------------------------
+    // count < 0: population unknown on the host (device-driven persistent grid)
+    template <class Src>
+    static void launch_sym_tier(const Ctx &cx, const typename Src::Args &sa, TierCommon c, int t,
+                                int count, cudaStream_t st) {
+        c.tier = t;
+        const int T = 2 * tier_cap(t);
+        if (t <= 2) {
+            const int want = count < 0 ? cx.nsm * 8 : (count + 7) / 8;
+            const int blocks = std::max(1, std::min(want, cx.nsm * 8));
+            if (T == 64) k_sym_warp<Src, 64><<<blocks, 256, 0, st>>>(sa, c);
+            else k_sym_warp<Src, 256><<<blocks, 256, 0, st>>>(sa, c);
+            return;
+        }
+        const int thr = block_tier_threads(T, cx.tun);
+        const int smem = T * 4;
+        const int per_sm = std::max(1, std::min(2048 / thr, (200 * 1024) / smem));
+        const int want = count < 0 ? cx.nsm * per_sm : count;
+        const int blocks = std::max(1, std::min(want, cx.nsm * per_sm));
+        switch (T) {
+            case 512: k_sym_block<Src, 512><<<blocks, thr, smem, st>>>(sa, c); break;
+            case 1024: k_sym_block<Src, 1024><<<blocks, thr, smem, st>>>(sa, c); break;
+            case 2048: k_sym_block<Src, 2048><<<blocks, thr, smem, st>>>(sa, c); break;
+            case 4096: k_sym_block<Src, 4096><<<blocks, thr, smem, st>>>(sa, c); break;
+            case 8192: k_sym_block<Src, 8192><<<blocks, thr, smem, st>>>(sa, c); break;
+            default: k_sym_block<Src, 16384><<<blocks, thr, smem, st>>>(sa, c); break;
+        }
+    }
+
+    template <class Src>
+    static void launch_num_tier(const Ctx &cx, const typename Src::Args &sa, TierCommon c, int t,
+                                int count, I *rows, V *vals, cudaStream_t st) {
+        c.tier = t;
+        const int T = 2 * tier_cap(t);
+        if (t <= 2) {
+            const int want = count < 0 ? cx.nsm * 8 : (count + 7) / 8;
+            const int blocks = std::max(1, std::min(want, cx.nsm * 8));
+            if (T == 64) k_num_warp<Src, 64><<<blocks, 256, 0, st>>>(sa, c, rows, vals);
+            else k_num_warp<Src, 256><<<blocks, 256, 0, st>>>(sa, c, rows, vals);
+            return;
+        }
+        const int thr = block_tier_threads(T, cx.tun);
+        const int smem = T * (int)(4 + sizeof(V));
+        const int per_sm = std::max(1, std::min(2048 / thr, (220 * 1024) / smem));
+        const int want = count < 0 ? cx.nsm * per_sm : count;
+        const int blocks = std::max(1, std::min(want, cx.nsm * per_sm));
+        switch (T) {
+            case 512: k_num_block<Src, 512><<<blocks, thr, smem, st>>>(sa, c, rows, vals); break;
+            case 1024: k_num_block<Src, 1024><<<blocks, thr, smem, st>>>(sa, c, rows, vals); break;
+            case 2048: k_num_block<Src, 2048><<<blocks, thr, smem, st>>>(sa, c, rows, vals); break;
+            case 4096: k_num_block<Src, 4096><<<blocks, thr, smem, st>>>(sa, c, rows, vals); break;
+            case 8192: k_num_block<Src, 8192><<<blocks, thr, smem, st>>>(sa, c, rows, vals); break;
+            default: k_num_block<Src, 16384><<<blocks, thr, smem, st>>>(sa, c, rows, vals); break;
+        }
+    }
+
+    static int dense_smem(const Ctx &cx) {
+        const int R = 1 << cx.tun.log2R;
+        return R * (int)sizeof(V) + R / 8;
+    }
+
+    // ---- symbolic pass -------------------------------------------------------
+    // Bins columns [c_lo, c_hi) of the source, counts distinct rows into
+    // cnt_out, fills list/off; heavy columns get per-panel counts in pcnt.
+    // heavy_ord_w (optional) receives the heavy ordinals (full pass only).
+    template <class Src>
+    static spgemm_status sym_pass(const Ctx &cx, const typename Src::Args &sa, int64_t c_lo, int64_t c_hi,
+                           const int64_t *bound, int64_t *f_out, uint8_t *tier, int64_t *cnt_out,
+                           int32_t *list, int32_t *off, int32_t *heavy_ord_w,
+                           const int32_t *heavy_ord_r, DevBuf *pcnt_grow, int32_t *pcnt_ptr,
+                           int *hist_out, cudaStream_t st) {
+        const int64_t nc = c_hi - c_lo;
+        SPG_CK(cudaMemsetAsync(cx.hist, 0, sizeof(int32_t) * 64, st));
+        SPG_CK(cudaMemsetAsync(cx.cursor, 0, sizeof(int32_t) * 64, st));
+        if (nc > 0) {
+            k_flops_bin<Src><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
+                sa, c_lo, c_hi, cx.tun.hash_cap_max, bound, f_out, tier, cnt_out, cx.hist);
+            k_bin_scatter<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(tier, c_lo, c_hi, cx.hist,
+                                                                       cx.cursor, list, off,
+                                                                       heavy_ord_w);
+            SPG_CK(cudaGetLastError());
+        }
+        SPG_CK(cudaMemcpyAsync(cx.h_small, cx.hist, sizeof(int32_t) * 16, cudaMemcpyDeviceToHost, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        int hist[16];
+        std::memcpy(hist, cx.h_small, sizeof(hist));
+        if (nc <= 0) std::memset(hist, 0, sizeof(hist));
+        if (hist_out) std::memcpy(hist_out, hist, sizeof(hist));
+        int nheavy = 0;
+        for (int t = kHeavyTier0; t < kTiers; ++t) nheavy += hist[t];
+        TierCommon c = common_of(cx);
+        c.list = list; c.list_off = off; c.cnt = cnt_out;
+        for (int t = 1; t <= 8; ++t)
+            if (hist[t]) launch_sym_tier<Src>(cx, sa, c, t, hist[t], st);
+        if (nheavy) {
+            if (pcnt_grow) {
+                SPG_CK(pcnt_grow->ensure(sizeof(int32_t) * (size_t)nheavy * cx.P));
+                pcnt_ptr = pcnt_grow->as<int32_t>();
+            }
+            c.pcnt = pcnt_ptr;
+            c.heavy_ord = heavy_ord_r;
+            const int64_t items = (int64_t)nheavy * cx.Q;
+            const int smem = (int)(((cx.Rs + 31) / 32) * 4);
+            const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(items, cx.nsm));
+            k_sym_bitmap<Src><<<blocks, 1024, smem, st>>>(sa, c);
+        }
+        SPG_CK(cudaGetLastError());
+        return SPGEMM_OK;
+    }
+
+    // ---- numeric pass --------------------------------------------------------
+    // tc: host tier populations (nullptr: device-driven grids). heavy: whether
+    // dense items exist. sym_list/sym_off: the symbolic heavy list.
+    template <class Src, class DSrc>
+    static spgemm_status num_pass(const Ctx &cx, const typename Src::Args &sa,
+                           const typename DSrc::Args &da, int64_t c_lo, int64_t c_hi,
+                           const int64_t *cnt, const int64_t *dense_sel, const NumOut<I, V> &o,
+                           const int *tc, bool heavy, const int32_t *sym_list,
+                           const int32_t *sym_off, const int32_t *heavy_ord,
+                           const int32_t *pcnt_in, uint8_t *tier, int32_t *list, int32_t *off,
+                           cudaStream_t st) {
+        const int64_t nc = c_hi - c_lo;
+        bool any_hash = tc == nullptr;
+        if (tc) for (int t = 1; t <= 8; ++t) any_hash |= tc[t] > 0;
+        TierCommon c = common_of(cx);
+        c.colptr = o.colptr;
+        c.out_base = o.out_base;
+        if (any_hash && nc > 0) {
+            SPG_CK(cudaMemsetAsync(cx.hist, 0, sizeof(int32_t) * 64, st));
+            SPG_CK(cudaMemsetAsync(cx.cursor, 0, sizeof(int32_t) * 64, st));
+            k_numeric_tier<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
+                cnt, dense_sel, c_lo, c_hi, cx.tun.hash_cap_max, tier, cx.hist);
+            k_bin_scatter<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
+                tier, c_lo, c_hi, cx.hist, cx.cursor, list, off, nullptr);
+            SPG_CK(cudaGetLastError());
+            c.list = list; c.list_off = off;
+            for (int t = 1; t <= 8; ++t) {
+                if (tier_cap(t) > cx.tun.hash_cap_max) break;
+                const int cntt = tc ? tc[t] : -1;
+                if (cntt != 0) launch_num_tier<Src>(cx, sa, c, t, cntt, o.rows, o.vals, st);
+            }
+        }
+        if (heavy) {
+            c.list = sym_list; c.list_off = sym_off;
+            c.dense_sel = dense_sel;
+            c.heavy_ord = heavy_ord;
+            c.pcnt_in = pcnt_in;
+            c.c_lo = c_lo; c.c_hi = c_hi;
+            const int smem = dense_smem(cx);
+            const int per_sm = std::max(1, std::min(2, (220 * 1024) / smem));
+            k_num_dense<DSrc><<<cx.nsm * per_sm, 1024, smem, st>>>(da, c, o.rows, o.vals);
+        }
+        SPG_CK(cudaGetLastError());
+        return SPGEMM_OK;
+    }
+
+    // ---- plan ----------------------------------------------------------------
+    GA gemm_args(PlanState &ps, int64_t k0, int64_t k1) {
+        GA a{};
+        a.probs = ps.probs.as<PD>();
+        a.nprob = 1;
+        a.k0 = k0; a.k1 = k1;
+        a.ap_end = ps.ap_end.as<int64_t>();
+        a.ap_row = ps.ap_row.as<uint16_t>();
+        a.ap_val = ps.ap_val.as<V>();
+        return a;
+    }
+
+    spgemm_status setup(PlanState &ps, cudaStream_t st) override {
+        attrs();
+        PD pd{};
+        pd.ap = (const I *)ps.A.colptr; pd.ai = (const I *)ps.A.rowidx; pd.av = (const V *)ps.A.vals;
+        pd.bp = (const I *)ps.B.colptr; pd.bi = (const I *)ps.B.rowidx; pd.bv = (const V *)ps.B.vals;
+        pd.m = ps.m; pd.gcol0 = 0; pd.ncols = ps.n; pd.ka = ps.k;
+        SPG_CK(ps.probs.ensure(sizeof(PD)));
+        SPG_CK(cudaMemcpyAsync(ps.probs.p, &pd, sizeof(PD), cudaMemcpyHostToDevice, st));
+        const int64_t n = ps.n;
+        SPG_CK(ps.f.ensure(sizeof(int64_t) * (n + 1)));
+        SPG_CK(ps.cnt.ensure(sizeof(int64_t) * (n + 1)));
+        SPG_CK(ps.colptr.ensure(sizeof(int64_t) * (n + 1)));
+        SPG_CK(ps.wbytes.ensure(sizeof(int64_t) * (n + 1)));
+        SPG_CK(ps.tier.ensure(n + 16));
+        SPG_CK(ps.list_sym.ensure(sizeof(int32_t) * (n + 1)));
+        SPG_CK(ps.list_num.ensure(sizeof(int32_t) * (n + 1)));
+        SPG_CK(ps.heavy_ord.ensure(sizeof(int32_t) * (n + 1)));
+        SPG_CK(ps.hist.ensure(sizeof(int32_t) * 64));
+        SPG_CK(ps.cursor.ensure(sizeof(int32_t) * 64));
+        SPG_CK(ps.off_sym.ensure(sizeof(int32_t) * 64));
+        SPG_CK(ps.off_num.ensure(sizeof(int32_t) * 64));
+        SPG_CK(ps.err.ensure(sizeof(int) * 4));
+        SPG_CK(ps.scan_part.ensure(sizeof(int64_t) * scan_partials_len(n + 1)));
+        SPG_CK(ps.h_colptr.ensure(sizeof(int64_t) * (n + 1)));
+        SPG_CK(ps.h_small.ensure(4096));
+        SPG_CK(cudaMemsetAsync(ps.err.p, 0, sizeof(int) * 4, st));
+        if (ps.s > 1) {
+            SPG_CK(ps.stage_cnt.ensure(sizeof(int64_t) * (size_t)ps.s * (n + 1)));
+            SPG_CK(ps.stage_colptr.ensure(sizeof(int64_t) * (size_t)ps.s * (n + 1)));
+            SPG_CK(ps.h_stage_colptr.ensure(sizeof(int64_t) * (size_t)ps.s * (n + 1)));
+        }
+        return SPGEMM_OK;
+    }
+
+    spgemm_status symbolic(PlanState &ps, cudaStream_t st) override {
+        const int64_t n = ps.n;
+        ps.have_symbolic = false;
+        ps.panels_built = false;
+        Ctx cx = make_ctx(ps);
+        SPG_CK(cudaMemsetAsync(ps.err.p, 0, sizeof(int) * 4, st));
+        // full product: flops, counts, heavy list
+        SPG_ST(sym_pass<SrcGemm<I, V>>(cx, gemm_args(ps, 0, ps.k), 0, n, nullptr, ps.f.as<int64_t>(),
+                                       ps.tier.as<uint8_t>(), ps.cnt.as<int64_t>(),
+                                       ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
+                                       ps.heavy_ord.as<int32_t>(), ps.heavy_ord.as<int32_t>(),
+                                       &ps.pcnt, nullptr, ps.sym_hist, st));
+        ps.nheavy = 0;
+        for (int t = kHeavyTier0; t < kTiers; ++t) ps.nheavy += ps.sym_hist[t];
+        SPG_CK(exclusive_scan_i64(ps.cnt.as<int64_t>(), n, ps.colptr.as<int64_t>(),
+                                  ps.scan_part.as<int64_t>(), 1, st));
+        // k-split stages: per-stage counts nnz(D_t(:, j)) (LocalSymbolic per stage,
+        // Algorithm 3), panel counts for the heavy columns
+        if (ps.s > 1) {
+            if (ps.nheavy)
+                SPG_CK(ps.stage_pcnt.ensure(sizeof(int32_t) * (size_t)ps.s * ps.nheavy * ps.P));
+            for (int t = 0; t < ps.s; ++t) {
+                const int64_t k0 = (int64_t)t * ps.k / ps.s, k1 = (int64_t)(t + 1) * ps.k / ps.s;
+                int64_t *scnt = ps.stage_cnt.as<int64_t>() + (size_t)t * (n + 1);
+                int32_t *spc = ps.nheavy ? ps.stage_pcnt.as<int32_t>() + (size_t)t * ps.nheavy * ps.P
+                                         : nullptr;
+                SPG_ST(sym_pass<SrcGemm<I, V>>(cx, gemm_args(ps, k0, k1), 0, n, ps.cnt.as<int64_t>(),
+                                               nullptr, ps.tier.as<uint8_t>(), scnt,
+                                               ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(),
+                                               nullptr, ps.heavy_ord.as<int32_t>(), nullptr, spc,
+                                               nullptr, st));
+                SPG_CK(exclusive_scan_i64(scnt, n, ps.stage_colptr.as<int64_t>() + (size_t)t * (n + 1),
+                                          ps.scan_part.as<int64_t>(), 1, st));
+            }
+            SPG_CK(cudaMemcpyAsync(ps.h_stage_colptr.p, ps.stage_colptr.p,
+                                   sizeof(int64_t) * (size_t)ps.s * (n + 1), cudaMemcpyDeviceToHost, st));
+        }
+        SPG_CK(cudaMemcpyAsync(ps.h_colptr.p, ps.colptr.p, sizeof(int64_t) * (n + 1),
+                               cudaMemcpyDeviceToHost, st));
+        SPG_CK(cudaMemcpyAsync(ps.h_small.as<char>() + 256, ps.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SPG_CK(exclusive_scan_i64(ps.f.as<int64_t>(), n, ps.wbytes.as<int64_t>(),
+                                  ps.scan_part.as<int64_t>(), 1, st));
+        SPG_CK(cudaMemcpyAsync(ps.h_small.as<char>() + 512, ps.wbytes.as<int64_t>() + n, sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, st));
+        if (ps.nheavy) SPG_ST(build_panels(ps, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        const int errw = *(int *)(ps.h_small.as<char>() + 256);
+        if (errw) {
+            set_error("symbolic: device error flags " + std::to_string(errw));
+            return SPGEMM_ERR_OVERFLOW;
+        }
+        ps.flops = *(int64_t *)(ps.h_small.as<char>() + 512);
+        ps.nnz_c = ps.h_colptr.as<int64_t>()[n];
+        SPG_ST(plan_batches(ps));
+        if (ps.s > 1) SPG_ST(setup_stage_buffers(ps, st));
+        ps.have_symbolic = true;
+        return SPGEMM_OK;
+    }
+
+    spgemm_status build_panels(PlanState &ps, cudaStream_t st) {
+        const int64_t ka = ps.k;
+        const int64_t N = (int64_t)ps.P * ka;
+        const int64_t nnzA = ps.A.nnz;
+        SPG_CK(ps.ap_end.ensure(sizeof(int64_t) * (N + 1)));
+        SPG_CK(ps.ap_row.ensure(sizeof(uint16_t) * (nnzA + 8)));
+        SPG_CK(ps.ap_val.ensure(sizeof(V) * (nnzA + 8)));
+        SPG_CK(ps.merge_tmp.ensure(sizeof(int64_t) * scan_partials_len(N + 1)));
+        SPG_CK(cudaMemsetAsync(ps.ap_end.p, 0, sizeof(int64_t) * (N + 1), st));
+        const int blocks = ps.nsm * 8;
+        k_panel_count<I><<<blocks, 256, 0, st>>>((const I *)ps.A.colptr, (const I *)ps.A.rowidx, ka,
+                                                 ps.tun.log2R, ps.ap_end.as<unsigned long long>());
+        SPG_CK(exclusive_scan_i64(ps.ap_end.as<int64_t>(), N, ps.ap_end.as<int64_t>(),
+                                  ps.merge_tmp.as<int64_t>(), 0, st));
+        k_panel_scatter<I, V><<<blocks, 256, 0, st>>>((const I *)ps.A.colptr, (const I *)ps.A.rowidx,
+                                                      (const V *)ps.A.vals, ka, ps.tun.log2R,
+                                                      ps.ap_end.as<unsigned long long>(),
+                                                      ps.ap_row.as<uint16_t>(), ps.ap_val.as<V>());
+        SPG_CK(cudaGetLastError());
+        ps.panels_built = true;
+        return SPGEMM_OK;
+    }
+
+    static void tier_counts(const int64_t *cp, const int64_t *sel, int64_t c0, int64_t c1, int capmax,
+                            std::array<int, 16> &tc, int64_t *heavy) {
+        tc.fill(0);
+        int64_t hv = 0;
+        for (int64_t j = c0; j < c1; ++j) {
+            const int64_t x = cp[j + 1] - cp[j];
+            const int64_t s = sel ? sel[j + 1] - sel[j] : x;
+            if (s > capmax) { ++hv; continue; }
+            if (x == 0) continue;
+            for (int t = 1; t <= 8; ++t) {
+                if (tier_cap(t) > capmax) break;
+                if (x <= tier_cap(t)) { tc[t]++; break; }
+            }
+        }
+        if (heavy) *heavy = hv;
+    }
+
+    // Greedy contiguous column ranges under the per-batch cap, from the exact
+    // per-column counts (Eq. (2)'s smallest b for contiguous ranges).
+    spgemm_status plan_batches(PlanState &ps) {
+        const int64_t n = ps.n;
+        const int64_t *hc = ps.h_colptr.as<int64_t>();
+        const int64_t *hs = ps.s > 1 ? ps.h_stage_colptr.as<int64_t>() : nullptr;
+        const int64_t r = (ps.idx64 ? 8 : 4) + (ps.vtype == SPGEMM_F32 ? 4 : 8);
+        ps.bytes_per_nnz = r;
+        const int64_t ptr_bytes = 8;
+        const int64_t inputs = (int64_t)(ps.A.nnz + ps.B.nnz) * r +
+                               (ps.A.ncols + 1 + ps.B.ncols + 1) * (ps.idx64 ? 8 : 4);
+        const int64_t ws = (int64_t)ps.workspace_bytes();
+        const int64_t avail = (int64_t)ps.budget - inputs - ws;
+        const int ring = ps.opts.ring_depth > 0 ? ps.opts.ring_depth : 2;
+        if (avail <= 0) {
+            set_error("budget " + std::to_string(ps.budget) + " B does not cover the inputs (" +
+                      std::to_string(inputs) + " B) and the workspace (" + std::to_string(ws) + " B)");
+            return SPGEMM_ERR_BUDGET;
+        }
+        const int64_t cap = avail / ring;
+        ps.batch_cap = cap;
+        ps.batches.clear();
+        // unmerged entries up to column j: sum over stages of the stage colptrs
+        auto unm = [&](int64_t j) {
+            if (!hs) return (int64_t)0;
+            int64_t u = 0;
+            for (int t = 0; t < ps.s; ++t) u += hs[(size_t)t * (n + 1) + j];
+            return u;
+        };
+        auto wprefix = [&](int64_t j) { return r * (hc[j] + unm(j)) + ptr_bytes * j; };
+        int64_t c = 0;
+        if (n == 0) {
+            Batch b;
+            b.tc.resize(ps.s > 1 ? ps.s + 1 : 1);
+            for (auto &x : b.tc) x.fill(0);
+            ps.batches.push_back(b);
+        }
+        while (c < n) {
+            const int64_t limit = wprefix(c) + cap;
+            int64_t lo = c, hi = n;
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo + 1) / 2;
+                if (wprefix(mid) <= limit) lo = mid; else hi = mid - 1;
+            }
+            if (lo == c) {
+                set_error("column " + std::to_string(c) + " needs " +
+                          std::to_string(wprefix(c + 1) - wprefix(c)) +
+                          " B, more than one batch may hold (" + std::to_string(cap) + " B)");
+                return SPGEMM_ERR_BUDGET;
+            }
+            Batch b;
+            b.c0 = c; b.c1 = lo; b.nnz = hc[lo] - hc[c];
+            b.unmerged = hs ? unm(lo) - unm(c) : b.nnz;
+            ps.batches.push_back(b);
+            c = lo;
+        }
+        const int capmax = ps.tun.hash_cap_max;
+        int64_t total_unm = 0;
+        for (auto &b : ps.batches) {
+            if (ps.s == 1) {
+                b.tc.resize(1);
+                tier_counts(hc, nullptr, b.c0, b.c1, capmax, b.tc[0], &b.heavy);
+            } else {
+                b.tc.resize(ps.s + 1);
+                tier_counts(hc, nullptr, b.c0, b.c1, capmax, b.tc[0], &b.heavy);
+                b.doff.resize(ps.s);
+                int64_t off = 0;
+                for (int t = 0; t < ps.s; ++t) {
+                    const int64_t *sc = hs + (size_t)t * (n + 1);
+                    tier_counts(sc, hc, b.c0, b.c1, capmax, b.tc[1 + t], nullptr);
+                    b.doff[t] = off;
+                    off += sc[b.c1] - sc[b.c0];
+                }
+            }
+            total_unm += b.unmerged;
+        }
+        ps.unmerged = ps.s > 1 ? total_unm : ps.nnz_c;
+        return SPGEMM_OK;
+    }
+
+    // Partial buffers and per-batch part tables for the k-split merge.
+    spgemm_status setup_stage_buffers(PlanState &ps, cudaStream_t st) {
+        int64_t mx = 0;
+        for (auto &b : ps.batches) mx = std::max(mx, b.unmerged);
+        SPG_CK(ps.drows.ensure(sizeof(I) * (size_t)(mx + 1)));
+        SPG_CK(ps.dvals.ensure(sizeof(V) * (size_t)(mx + 1)));
+        const size_t nb = ps.batches.size();
+        const size_t bytes = sizeof(PartDev<I, V>) * nb * ps.s;
+        SPG_CK(ps.parts_tab.ensure(bytes));
+        SPG_CK(ps.h_parts.ensure(bytes));
+        auto *tab = ps.h_parts.as<PartDev<I, V>>();
+        const int64_t *hs = ps.h_stage_colptr.as<int64_t>();
+        for (size_t bi = 0; bi < nb; ++bi) {
+            const Batch &b = ps.batches[bi];
+            for (int t = 0; t < ps.s; ++t) {
+                PartDev<I, V> &p = tab[bi * ps.s + t];
+                p.colptr = ps.stage_colptr.as<int64_t>() + (size_t)t * (ps.n + 1);
+                p.ptr64 = 1;
+                p.sub = hs[(size_t)t * (ps.n + 1) + b.c0] - b.doff[t];
+                p.rows = ps.drows.as<I>();
+                p.vals = ps.dvals.as<V>();
+                p.pcnt = ps.nheavy ? ps.stage_pcnt.as<int32_t>() + (size_t)t * ps.nheavy * ps.P : nullptr;
+            }
+        }
+        SPG_CK(cudaMemcpyAsync(ps.parts_tab.p, ps.h_parts.p, bytes, cudaMemcpyHostToDevice, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        return SPGEMM_OK;
+    }
+
+    // ---- numeric -------------------------------------------------------------
+    spgemm_status numeric(PlanState &ps, int64_t t, spgemm_csc *C, cudaStream_t st) override {
+        const Batch &b = ps.batches[(size_t)t];
+        Ctx cx = make_ctx(ps);
+        const int64_t n = ps.n;
+        const int64_t *hc = ps.h_colptr.as<int64_t>();
+        if (ps.s == 1) {
+            NumOut<I, V> o{ps.colptr.as<int64_t>(), hc[b.c0], (I *)C->rowidx, (V *)C->vals};
+            GA ga = gemm_args(ps, 0, ps.k);
+            SPG_ST((num_pass<SrcGemm<I, V>, SrcPanel<I, V>>(
+                cx, ga, ga, b.c0, b.c1, ps.cnt.as<int64_t>(), ps.cnt.as<int64_t>(), o, b.tc[0].data(),
+                b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
+                ps.heavy_ord.as<int32_t>(), ps.pcnt.as<int32_t>(), ps.tier.as<uint8_t>(),
+                ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st)));
+        } else {
+            const int64_t *hs = ps.h_stage_colptr.as<int64_t>();
+            for (int s = 0; s < ps.s; ++s) {
+                const int64_t k0 = (int64_t)s * ps.k / ps.s, k1 = (int64_t)(s + 1) * ps.k / ps.s;
+                const int64_t *scp = ps.stage_colptr.as<int64_t>() + (size_t)s * (n + 1);
+                const int64_t *scnt = ps.stage_cnt.as<int64_t>() + (size_t)s * (n + 1);
+                NumOut<I, V> o{scp, hs[(size_t)s * (n + 1) + b.c0] - b.doff[s], ps.drows.as<I>(),
+                               ps.dvals.as<V>()};
+                GA ga = gemm_args(ps, k0, k1);
+                const int32_t *spc = ps.nheavy ? ps.stage_pcnt.as<int32_t>() + (size_t)s * ps.nheavy * ps.P
+                                               : nullptr;
+                SPG_ST((num_pass<SrcGemm<I, V>, SrcPanel<I, V>>(
+                    cx, ga, ga, b.c0, b.c1, scnt, ps.cnt.as<int64_t>(), o, b.tc[1 + s].data(),
+                    b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
+                    ps.heavy_ord.as<int32_t>(), spc, ps.tier.as<uint8_t>(), ps.list_num.as<int32_t>(),
+                    ps.off_num.as<int32_t>(), st)));
+            }
+            // sort-free hash merge of the stage partials (Sec. IV-D)
+            PA pa{ps.parts_tab.as<PartDev<I, V>>() + (size_t)t * ps.s, ps.s, ps.m};
+            NumOut<I, V> o{ps.colptr.as<int64_t>(), hc[b.c0], (I *)C->rowidx, (V *)C->vals};
+            SPG_ST((num_pass<SrcParts<I, V>, SrcPartsPanel<I, V>>(
+                cx, pa, pa, b.c0, b.c1, ps.cnt.as<int64_t>(), ps.cnt.as<int64_t>(), o, b.tc[0].data(),
+                b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
+                ps.heavy_ord.as<int32_t>(), ps.pcnt.as<int32_t>(), ps.tier.as<uint8_t>(),
+                ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st)));
+        }
+        SPG_CK(rebase_colptr(ps.colptr.as<int64_t>() + b.c0, b.c1 - b.c0, C->colptr,
+                             C->ptr_type == SPGEMM_I64, st));
+        return SPGEMM_OK;
+    }
+
+    // ---- backward ------------------------------------------------------------
+    spgemm_status backward(PlanState &ps, const spgemm_csc *G, void *dA, void *dB,
+                           cudaStream_t st) override {
+        if (ps.vtype == SPGEMM_INT64) {
+            set_error("backward needs floating-point values");
+            return SPGEMM_ERR_INVALID;
+        }
+        Ctx cx = make_ctx(ps);
+        const int64_t n = ps.n;
+        GradArgs<I, V> ga{};
+        ga.gemm = gemm_args(ps, 0, ps.k);
+        ga.gcolptr = G->colptr;
+        ga.gptr64 = G->ptr_type == SPGEMM_I64;
+        ga.grows = (const I *)G->rowidx;
+        ga.gvals = (const V *)G->vals;
+        ga.dA = (V *)dA;
+        ga.dB = (V *)dB;
+        if (ps.A.nnz)
+            k_fill_zero<V><<<(unsigned)((ps.A.nnz + 255) / 256), 256, 0, st>>>((V *)dA, ps.A.nnz);
+        if (ps.B.nnz)
+            k_fill_zero<V><<<(unsigned)((ps.B.nnz + 255) / 256), 256, 0, st>>>((V *)dB, ps.B.nnz);
+        if (n == 0) return SPGEMM_OK;
+        SPG_CK(cudaMemsetAsync(cx.hist, 0, sizeof(int32_t) * 64, st));
+        SPG_CK(cudaMemsetAsync(cx.cursor, 0, sizeof(int32_t) * 64, st));
+        k_bwd_tier<I, V><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ga, n, cx.tun.hash_cap_max,
+                                                                       ps.tier.as<uint8_t>(), cx.hist);
+        k_bin_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+            ps.tier.as<uint8_t>(), 0, n, cx.hist, cx.cursor, ps.list_num.as<int32_t>(),
+            ps.off_num.as<int32_t>(), nullptr);
+        SPG_CK(cudaMemcpyAsync(cx.h_small, cx.hist, sizeof(int32_t) * 16, cudaMemcpyDeviceToHost, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        int hist[16];
+        std::memcpy(hist, cx.h_small, sizeof(hist));
+        TierCommon c = common_of(cx);
+        c.list = ps.list_num.as<int32_t>();
+        c.list_off = ps.off_num.as<int32_t>();
+        for (int t = 1; t <= 8; ++t) {
+            if (!hist[t]) continue;
+            c.tier = t;
+            const int T = 2 * tier_cap(t);
+            if (t <= 2) {
+                const int blocks = std::max(1, std::min((hist[t] + 7) / 8, cx.nsm * 8));
+                if (T == 64) k_bwd_warp<I, V, 64><<<blocks, 256, 0, st>>>(ga, c);
+                else k_bwd_warp<I, V, 256><<<blocks, 256, 0, st>>>(ga, c);
+                continue;
+            }
+            const int thr = block_tier_threads(T, cx.tun);
+            const int smem = T * (int)(4 + sizeof(V));
+            const int per_sm = std::max(1, std::min(2048 / thr, (220 * 1024) / smem));
+            const int blocks = std::max(1, std::min(hist[t], cx.nsm * per_sm));
+            switch (T) {
+                case 512: k_bwd_block<I, V, 512><<<blocks, thr, smem, st>>>(ga, c); break;
+                case 1024: k_bwd_block<I, V, 1024><<<blocks, thr, smem, st>>>(ga, c); break;
+                case 2048: k_bwd_block<I, V, 2048><<<blocks, thr, smem, st>>>(ga, c); break;
+                case 4096: k_bwd_block<I, V, 4096><<<blocks, thr, smem, st>>>(ga, c); break;
+                case 8192: k_bwd_block<I, V, 8192><<<blocks, thr, smem, st>>>(ga, c); break;
+                default: k_bwd_block<I, V, 16384><<<blocks, thr, smem, st>>>(ga, c); break;
+            }
+        }
+        int nheavy = 0;
+        for (int t = kHeavyTier0; t < kTiers; ++t) nheavy += hist[t];
+        if (nheavy) {
+            const int smem = dense_smem(cx);
+            k_bwd_dense<I, V><<<cx.nsm, 1024, smem, st>>>(ga, c);
+        }
+        SPG_CK(cudaGetLastError());
+        return SPGEMM_OK;
+    }
+
+    // ---- standalone merge (spgemm_merge) ---------------------------------------
+    static spgemm_status merge(const spgemm_csc *parts, int nparts, spgemm_csc *out, cudaStream_t st) {
+        attrs();
+        const int64_t n = parts[0].ncols, m = parts[0].nrows;
+        int dev = 0;
+        cudaDeviceProp prop;
+        SPG_CK(cudaGetDevice(&dev));
+        SPG_CK(cudaGetDeviceProperties(&prop, dev));
+        PlanState tmp;   // scratch only
+        tmp.nsm = prop.multiProcessorCount;
+        tmp.tun.log2R = sizeof(V) == 4 ? 15 : 14;
+        const int64_t R = 1ll << tmp.tun.log2R;
+        tmp.P = (int)std::max<int64_t>(1, (m + R - 1) / R);
+        const int64_t maxbm = (int64_t)(192 * 1024) * 8;
+        const int64_t mpad = ((m + R - 1) / R) * R;
+        tmp.Rs = mpad <= maxbm ? (mpad > 0 ? mpad : R) : (maxbm / R) * R;
+        tmp.Q = (int)std::max<int64_t>(1, (m + tmp.Rs - 1) / tmp.Rs);
+        struct Guard { PlanState &p; ~Guard() { p.release_all(); } } guard{tmp};
+        std::vector<PartDev<I, V>> tab(nparts);
+        for (int i = 0; i < nparts; ++i) {
+            tab[i].colptr = parts[i].colptr;
+            tab[i].ptr64 = parts[i].ptr_type == SPGEMM_I64;
+            tab[i].sub = 0;
+            tab[i].rows = (const I *)parts[i].rowidx;
+            tab[i].vals = (const V *)parts[i].vals;
+            tab[i].pcnt = nullptr;
+        }
+        SPG_CK(tmp.parts_tab.ensure(sizeof(PartDev<I, V>) * nparts));
+        SPG_CK(tmp.cnt.ensure(sizeof(int64_t) * (n + 1)));
+        SPG_CK(tmp.colptr.ensure(sizeof(int64_t) * (n + 1)));
+        SPG_CK(tmp.tier.ensure(n + 16));
+        SPG_CK(tmp.list_sym.ensure(sizeof(int32_t) * (n + 1)));
+        SPG_CK(tmp.list_num.ensure(sizeof(int32_t) * (n + 1)));
+        SPG_CK(tmp.heavy_ord.ensure(sizeof(int32_t) * (n + 1)));
+        SPG_CK(tmp.hist.ensure(sizeof(int32_t) * 64));
+        SPG_CK(tmp.cursor.ensure(sizeof(int32_t) * 64));
+        SPG_CK(tmp.off_sym.ensure(sizeof(int32_t) * 64));
+        SPG_CK(tmp.off_num.ensure(sizeof(int32_t) * 64));
+        SPG_CK(tmp.err.ensure(sizeof(int) * 4));
+        SPG_CK(tmp.scan_part.ensure(sizeof(int64_t) * scan_partials_len(n + 1)));
+        SPG_CK(tmp.h_small.ensure(4096));
+        SPG_CK(cudaMemcpyAsync(tmp.parts_tab.p, tab.data(), sizeof(PartDev<I, V>) * nparts,
+                               cudaMemcpyHostToDevice, st));
+        SPG_CK(cudaMemsetAsync(tmp.err.p, 0, sizeof(int) * 4, st));
+        Ctx cx = make_ctx(tmp);
+        PA pa{tmp.parts_tab.as<PartDev<I, V>>(), nparts, m};
+        int hist[16];
+        SPG_ST(sym_pass<SrcParts<I, V>>(cx, pa, 0, n, nullptr, nullptr, tmp.tier.as<uint8_t>(),
+                                        tmp.cnt.as<int64_t>(), tmp.list_sym.as<int32_t>(),
+                                        tmp.off_sym.as<int32_t>(), tmp.heavy_ord.as<int32_t>(),
+                                        tmp.heavy_ord.as<int32_t>(), &tmp.pcnt, nullptr, hist, st));
+        SPG_CK(exclusive_scan_i64(tmp.cnt.as<int64_t>(), n, tmp.colptr.as<int64_t>(),
+                                  tmp.scan_part.as<int64_t>(), 1, st));
+        int64_t nnz = 0;
+        SPG_CK(cudaMemcpyAsync(&nnz, tmp.colptr.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        if (out->ptr_type == SPGEMM_I32 && nnz > 0x7fffffffLL) {
+            set_error("merged nnz does not fit a 32-bit colptr");
+            return SPGEMM_ERR_INDEX_OVERFLOW;
+        }
+        if (!out->rowidx) {
+            SPG_CK(rebase_colptr(tmp.colptr.as<int64_t>(), n, out->colptr, out->ptr_type == SPGEMM_I64, st));
+            out->nnz = nnz;
+            SPG_CK(cudaStreamSynchronize(st));
+            return SPGEMM_OK;
+        }
+        if (out->nnz != nnz) {
+            set_error("out->nnz does not match the merged size");
+            return SPGEMM_ERR_INVALID;
+        }
+        int nheavy = 0;
+        for (int t = kHeavyTier0; t < kTiers; ++t) nheavy += hist[t];
+        NumOut<I, V> o{tmp.colptr.as<int64_t>(), 0, (I *)out->rowidx, (V *)out->vals};
+        SPG_ST((num_pass<SrcParts<I, V>, SrcPartsPanel<I, V>>(
+            cx, pa, pa, 0, n, tmp.cnt.as<int64_t>(), tmp.cnt.as<int64_t>(), o, nullptr, nheavy > 0,
+            tmp.list_sym.as<int32_t>(), tmp.off_sym.as<int32_t>(), tmp.heavy_ord.as<int32_t>(),
+            tmp.pcnt.as<int32_t>(), tmp.tier.as<uint8_t>(), tmp.list_num.as<int32_t>(),
+            tmp.off_num.as<int32_t>(), st)));
+        int errw = 0;
+        SPG_CK(cudaMemcpyAsync(&errw, tmp.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        if (errw) {
+            set_error("merge: device error flags " + std::to_string(errw));
+            return SPGEMM_ERR_OVERFLOW;
+        }
+        return SPGEMM_OK;
+    }
+
+    // ---- many independent products (spgemm_multi) ------------------------------
+    static Ctx multi_ctx(MultiState &ms) {
+        Ctx c;
+        c.nsm = ms.nsm; c.tun = ms.tun; c.err = ms.err.as<int>();
+        c.hist = ms.hist.as<int32_t>(); c.cursor = ms.cursor.as<int32_t>();
+        c.h_small = ms.h_small.as<int32_t>();
+        c.P = 1; c.Q = 1; c.Rs = 32;
+        return c;
+    }
+
+    static GA multi_args(MultiState &ms) {
+        GA a{};
+        a.probs = ms.probs.as<PD>();
+        a.nprob = ms.nprob;
+        a.k0 = 0; a.k1 = INT64_MAX;
+        return a;
+    }
+
+    static spgemm_status multi_create(MultiState &ms, const spgemm_csc *As, const spgemm_csc *Bs,
+                                      cudaStream_t st) {
+        attrs();
+        std::vector<PD> tab(ms.nprob);
+        int64_t g = 0;
+        for (int i = 0; i < ms.nprob; ++i) {
+            PD &p = tab[i];
+            p.ap = (const I *)As[i].colptr; p.ai = (const I *)As[i].rowidx; p.av = (const V *)As[i].vals;
+            p.bp = (const I *)Bs[i].colptr; p.bi = (const I *)Bs[i].rowidx; p.bv = (const V *)Bs[i].vals;
+            p.m = As[i].nrows; p.gcol0 = g; p.ncols = Bs[i].ncols; p.ka = As[i].ncols;
+            g += Bs[i].ncols;
+        }
+        ms.total_cols = g;
+        const int64_t n = g;
+        SPG_CK(ms.probs.ensure(sizeof(PD) * ms.nprob));
+        SPG_CK(cudaMemcpyAsync(ms.probs.p, tab.data(), sizeof(PD) * ms.nprob, cudaMemcpyHostToDevice, st));
+        SPG_CK(ms.f.ensure(sizeof(int64_t) * (n + 1)));
+        SPG_CK(ms.cnt.ensure(sizeof(int64_t) * (n + 1)));
+        SPG_CK(ms.colptr.ensure(sizeof(int64_t) * (n + 1)));
+        SPG_CK(ms.tier.ensure(n + 16));
+        SPG_CK(ms.list.ensure(sizeof(int32_t) * (n + 1)));
+        SPG_CK(ms.list2.ensure(sizeof(int32_t) * (n + 1)));
+        SPG_CK(ms.off.ensure(sizeof(int32_t) * 64));
+        SPG_CK(ms.off2.ensure(sizeof(int32_t) * 64));
+        SPG_CK(ms.hist.ensure(sizeof(int32_t) * 64));
+        SPG_CK(ms.cursor.ensure(sizeof(int32_t) * 64));
+        SPG_CK(ms.err.ensure(sizeof(int) * 4));
+        SPG_CK(ms.scan_part.ensure(sizeof(int64_t) * scan_partials_len(n + 1)));
+        SPG_CK(ms.h_small.ensure(4096));
+        SPG_CK(cudaMemsetAsync(ms.err.p, 0, sizeof(int) * 4, st));
+        // flops of every column: arena capacity (nnz <= flops) and tier check
+        Ctx cx = multi_ctx(ms);
+        SPG_CK(cudaMemsetAsync(cx.hist, 0, sizeof(int32_t) * 64, st));
+        if (n > 0)
+            k_flops_bin<SrcGemm<I, V>><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                multi_args(ms), 0, n, cx.tun.hash_cap_max, nullptr, ms.f.as<int64_t>(),
+                ms.tier.as<uint8_t>(), ms.cnt.as<int64_t>(), cx.hist);
+        SPG_CK(cudaGetLastError());
+        SPG_CK(exclusive_scan_i64(ms.f.as<int64_t>(), n, ms.colptr.as<int64_t>(),
+                                  ms.scan_part.as<int64_t>(), 1, st));
+        SPG_CK(cudaMemcpyAsync(ms.h_small.p, cx.hist, sizeof(int32_t) * 16, cudaMemcpyDeviceToHost, st));
+        SPG_CK(cudaMemcpyAsync(ms.h_small.as<char>() + 256, ms.colptr.as<int64_t>() + n, sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        int hist[16];
+        std::memcpy(hist, ms.h_small.p, sizeof(hist));
+        for (int t = kHeavyTier0; t < kTiers; ++t)
+            if (n > 0 && hist[t]) {
+                set_error("a column of a batched problem may hold more than " +
+                          std::to_string(ms.tun.hash_cap_max) +
+                          " distinct rows; multiply that problem with a plan instead");
+                return SPGEMM_ERR_INVALID;
+            }
+        ms.total_flops = *(int64_t *)(ms.h_small.as<char>() + 256);
+        ms.capacity = ms.total_flops;
+        SPG_CK(ms.rows.ensure(sizeof(I) * (size_t)(ms.capacity + 1)));
+        SPG_CK(ms.vals.ensure(sizeof(V) * (size_t)(ms.capacity + 1)));
+        ms.enqueue = &multi_enqueue;
+        return SPGEMM_OK;
+    }
+
+    // flops, symbolic, scan and numeric for all problems; no host
+    // synchronisation (device-driven tier grids), so it can be captured.
+    static spgemm_status multi_enqueue(MultiState &ms, cudaStream_t st) {
+        Ctx cx = multi_ctx(ms);
+        const int64_t n = ms.total_cols;
+        GA ga = multi_args(ms);
+        SPG_CK(cudaMemsetAsync(cx.hist, 0, sizeof(int32_t) * 64, st));
+        SPG_CK(cudaMemsetAsync(cx.cursor, 0, sizeof(int32_t) * 64, st));
+        if (n > 0) {
+            k_flops_bin<SrcGemm<I, V>><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                ga, 0, n, cx.tun.hash_cap_max, nullptr, nullptr, ms.tier.as<uint8_t>(),
+                ms.cnt.as<int64_t>(), cx.hist);
+            k_bin_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                ms.tier.as<uint8_t>(), 0, n, cx.hist, cx.cursor, ms.list.as<int32_t>(),
+                ms.off.as<int32_t>(), nullptr);
+            TierCommon c = common_of(cx);
+            c.list = ms.list.as<int32_t>(); c.list_off = ms.off.as<int32_t>();
+            c.cnt = ms.cnt.as<int64_t>();
+            for (int t = 1; t <= 8; ++t) {
+                if (tier_cap(t) > cx.tun.hash_cap_max) break;
+                launch_sym_tier<SrcGemm<I, V>>(cx, ga, c, t, -1, st);
+            }
+        }
+        SPG_CK(cudaGetLastError());
+        SPG_CK(exclusive_scan_i64(ms.cnt.as<int64_t>(), n, ms.colptr.as<int64_t>(),
+                                  ms.scan_part.as<int64_t>(), 1, st));
+        NumOut<I, V> o{ms.colptr.as<int64_t>(), 0, ms.rows.as<I>(), ms.vals.as<V>()};
+        SPG_ST((num_pass<SrcGemm<I, V>, SrcPanel<I, V>>(
+            cx, ga, ga, 0, n, ms.cnt.as<int64_t>(), nullptr, o, nullptr, false, nullptr, nullptr,
+            nullptr, nullptr, ms.tier.as<uint8_t>(), ms.list2.as<int32_t>(), ms.off2.as<int32_t>(), st)));
+        return SPGEMM_OK;
+    }
+};
+
+}  // namespace spg

@@ -1,0 +1,51 @@
+// Dispatch on (index, value) type: one engine instantiation per pair.
+#include "plan.h"
+
+namespace spg {
+
+#define SPG_DECL(I, V)                                                                      \
+    EngineBase *make_engine_##I##_##V();                                                    \
+    spgemm_status merge_##I##_##V(const spgemm_csc *, int, spgemm_csc *, cudaStream_t);     \
+    spgemm_status multi_create_##I##_##V(MultiState &, const spgemm_csc *, const spgemm_csc *, \
+                                         cudaStream_t);
+SPG_DECL(i32, f64) SPG_DECL(i32, f32) SPG_DECL(i32, i64v)
+SPG_DECL(i64, f64) SPG_DECL(i64, f32) SPG_DECL(i64, i64v)
+
+#define SPG_SWITCH(idx64, vtype, CALL)                                 \
+    if (!(idx64)) {                                                    \
+        if ((vtype) == SPGEMM_F64) return CALL(i32, f64);              \
+        if ((vtype) == SPGEMM_F32) return CALL(i32, f32);              \
+        if ((vtype) == SPGEMM_INT64) return CALL(i32, i64v);           \
+    } else {                                                           \
+        if ((vtype) == SPGEMM_F64) return CALL(i64, f64);              \
+        if ((vtype) == SPGEMM_F32) return CALL(i64, f32);              \
+        if ((vtype) == SPGEMM_INT64) return CALL(i64, i64v);           \
+    }
+
+EngineBase *make_engine(int idx64, int vtype) {
+#define MK(I, V) make_engine_##I##_##V()
+    SPG_SWITCH(idx64, vtype, MK)
+#undef MK
+    return nullptr;
+}
+
+spgemm_status merge_dispatch(const spgemm_csc *parts, int nparts, spgemm_csc *out, cudaStream_t st) {
+    const int idx64 = parts[0].idx_type == SPGEMM_I64;
+    const int vtype = parts[0].val_type;
+#define MG(I, V) merge_##I##_##V(parts, nparts, out, st)
+    SPG_SWITCH(idx64, vtype, MG)
+#undef MG
+    set_error("unsupported type combination");
+    return SPGEMM_ERR_INVALID;
+}
+
+spgemm_status multi_create_typed(MultiState &ms, const spgemm_csc *As, const spgemm_csc *Bs,
+                                 cudaStream_t st) {
+#define MC(I, V) multi_create_##I##_##V(ms, As, Bs, st)
+    SPG_SWITCH(ms.idx64, ms.vtype, MC)
+#undef MC
+    set_error("unsupported type combination");
+    return SPGEMM_ERR_INVALID;
+}
+
+}  // namespace spg

@@ -1,0 +1,13 @@
+// Engine instantiation for int32_t indices and double values.
+#include "engine.cuh"
+
+namespace spg {
+EngineBase *make_engine_i32_f64() { return new Engine<int32_t, double>(); }
+spgemm_status merge_i32_f64(const spgemm_csc *p, int np, spgemm_csc *o, cudaStream_t st) {
+    return Engine<int32_t, double>::merge(p, np, o, st);
+}
+spgemm_status multi_create_i32_f64(MultiState &ms, const spgemm_csc *A, const spgemm_csc *B,
+                                     cudaStream_t st) {
+    return Engine<int32_t, double>::multi_create(ms, A, B, st);
+}
+}  // namespace spg

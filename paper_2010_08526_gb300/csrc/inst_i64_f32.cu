@@ -1,0 +1,13 @@
+// Engine instantiation for int64_t indices and float values.
+#include "engine.cuh"
+
+namespace spg {
+EngineBase *make_engine_i64_f32() { return new Engine<int64_t, float>(); }
+spgemm_status merge_i64_f32(const spgemm_csc *p, int np, spgemm_csc *o, cudaStream_t st) {
+    return Engine<int64_t, float>::merge(p, np, o, st);
+}
+spgemm_status multi_create_i64_f32(MultiState &ms, const spgemm_csc *A, const spgemm_csc *B,
+                                     cudaStream_t st) {
+    return Engine<int64_t, float>::multi_create(ms, A, B, st);
+}
+}  // namespace spg

@@ -1,0 +1,13 @@
+// Engine instantiation for int64_t indices and double values.
+#include "engine.cuh"
+
+namespace spg {
+EngineBase *make_engine_i64_f64() { return new Engine<int64_t, double>(); }
+spgemm_status merge_i64_f64(const spgemm_csc *p, int np, spgemm_csc *o, cudaStream_t st) {
+    return Engine<int64_t, double>::merge(p, np, o, st);
+}
+spgemm_status multi_create_i64_f64(MultiState &ms, const spgemm_csc *A, const spgemm_csc *B,
+                                     cudaStream_t st) {
+    return Engine<int64_t, double>::multi_create(ms, A, B, st);
+}
+}  // namespace spg

@@ -1,0 +1,984 @@
+// Device kernels of the SpGEMM hot path (templates; instantiated per index /
+// value type in inst_*.cu).
+//
+// Work decomposition. Every output column j is formed independently (the
+// column form of Gustavson's algorithm, Sec. II-C): C(:,j) = sum over
+// B(k,j) != 0 of A(:,k) B(k,j). A "source" describes where the contributions
+// (row, value) of column j come from:
+//   SrcGemm       -- the products A(i,k) B(k,j), walking A(:,k) for every
+//                    B(k,j) in a stage [k0, k1) of the inner dimension;
+//   SrcPanel      -- the same products restricted to one row panel, walking
+//                    a row-panelised copy of A;
+//   SrcParts      -- the entries of column j of several partial results (the
+//                    hash merge of Sec. IV-D);
+//   SrcPartsPanel -- the same restricted to one row panel, through per-panel
+//                    offsets of panel-grouped partial columns, or by filtering.
+// Columns are put in tiers by the number of distinct rows they can hold:
+//   warp tiers  : one warp per column, 2*cap-slot hash table (cap 32, 128);
+//   block tiers : one CTA per column, 2*cap-slot hash table (cap 256..8192);
+//   heavy tier  : symbolic -- a shared-memory bitmap over up to ~1.5M rows;
+//                 numeric  -- dense accumulation of one row panel in shared
+//                 memory per CTA.
+// Hash tables are sort-free (Sec. IV-D): rows are emitted in table order.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace spg {
+
+// ---------------------------------------------------------------------------
+// Problem table (one entry for a single product; many for batched products)
+// ---------------------------------------------------------------------------
+template <class I, class V> struct ProbDev {
+    const I *ap; const I *ai; const V *av;   // A: colptr, rowidx, vals
+    const I *bp; const I *bi; const V *bv;   // B
+    int64_t m;       // rows of A and C
+    int64_t gcol0;   // first global column of this problem
+    int64_t ncols;   // columns of this problem
+    int64_t ka;      // columns of A (inner dimension)
+};
+
+template <class I, class V>
+__device__ __forceinline__ int locate_prob(const ProbDev<I, V> *P, int nprob, int64_t g) {
+    if (nprob == 1) return 0;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P[mid].gcol0 <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One partial result of a merge: column g occupies
+// [colptr[g] - sub, colptr[g+1] - sub) of rows / vals.
+template <class I, class V> struct PartDev {
+    const void *colptr;
+    int ptr64;
+    int64_t sub;
+    const I *rows;
+    const V *vals;
+    const int32_t *pcnt;   // per-panel counts [nheavy * P] when columns are panel-grouped
+};
+
+// Arguments shared by all tier kernels (independent of the source).
+struct TierCommon {
+    const int32_t *list;     // global column ids, grouped by tier
+    const int32_t *list_off; // [kTiers+1] tier offsets in list (device)
+    int tier;
+    int short_seg, huge_seg;
+    int *err;
+    int64_t *cnt;            // symbolic output: per global column
+    const int64_t *colptr;   // numeric output offsets (global int64 colptr)
+    int64_t out_base;        // subtracted from colptr to index the output arrays
+    const int64_t *dense_sel;// dense numeric: columns with dense_sel[g] > hash_cap_max
+    int hash_cap_max;
+    const int32_t *heavy_ord;// heavy ordinal per global column
+    int32_t *pcnt;           // symbolic heavy output: per-panel counts [nheavy*P]
+    const int32_t *pcnt_in;  // dense numeric: per-panel counts of the output
+    int P, log2R;            // numeric panels: count and log2(rows)
+    int64_t Rs;              // symbolic bitmap rows per item
+    int Q;                   // symbolic panels per column
+    int64_t c_lo, c_hi;      // global column range (dense items)
+};
+
+template <class I, class V> struct GemmArgs {
+    const ProbDev<I, V> *probs;
+    int nprob;
+    int64_t k0, k1;
+    const int64_t *ap_end;   // row-panelised A: segment ends, index p*ka + c
+    const uint16_t *ap_row;  // local rows
+    const V *ap_val;
+};
+
+template <class I, class V> struct PartsArgs {
+    const PartDev<I, V> *parts;
+    int nparts;
+    int64_t m;
+};
+
+// ---------------------------------------------------------------------------
+// Sources
+// ---------------------------------------------------------------------------
+template <class I, class V> struct SrcGemm {
+    using Args = GemmArgs<I, V>;
+    using Val = V;
+    using Idx = I;
+    const ProbDev<I, V> *p;
+    int64_t b0, nb, k0, k1;
+    __device__ __forceinline__ void open(const Args &a, int64_t g) {
+        p = a.probs + locate_prob(a.probs, a.nprob, g);
+        const int64_t bc = g - p->gcol0;
+        b0 = (int64_t)p->bp[bc];
+        nb = (int64_t)p->bp[bc + 1] - b0;
+        k0 = a.k0; k1 = a.k1;
+    }
+    __device__ __forceinline__ int64_t nseg() const { return nb; }
+    __device__ __forceinline__ int64_t m() const { return p->m; }
+    __device__ __forceinline__ void seg(int64_t e, int64_t &beg, int &len, V &bv, int64_t &tag) const {
+        const int64_t pe = b0 + e;
+        const int64_t k = (int64_t)p->bi[pe];
+        if (k < k0 || k >= k1) { len = 0; return; }
+        const int64_t a0 = (int64_t)p->ap[k], a1 = (int64_t)p->ap[k + 1];
+        beg = a0; len = (int)(a1 - a0); bv = p->bv[pe]; tag = pe;
+    }
+    __device__ __forceinline__ uint32_t row(int64_t q) const { return (uint32_t)p->ai[q]; }
+    __device__ __forceinline__ V val(int64_t q, V bv) const { return mul_v(p->av[q], bv); }
+    // number of contributions (multiplications) of the column; warp-wide
+    __device__ __forceinline__ int64_t flops() const {
+        const int lane = threadIdx.x & 31;
+        int64_t s = 0;
+        for (int64_t e = lane; e < nb; e += 32) {
+            const int64_t k = (int64_t)p->bi[b0 + e];
+            if (k >= k0 && k < k1) s += (int64_t)p->ap[k + 1] - (int64_t)p->ap[k];
+        }
+        return warp_sum(s);
+    }
+};
+
+template <class I, class V> struct SrcParts {
+    using Args = PartsArgs<I, V>;
+    using Val = V;
+    using Idx = I;
+    static constexpr int kShift = 40;
+    const PartDev<I, V> *parts;
+    int nparts;
+    int64_t g, mm;
+    __device__ __forceinline__ void open(const Args &a, int64_t gg) {
+        parts = a.parts; nparts = a.nparts; g = gg; mm = a.m;
+    }
+    __device__ __forceinline__ int64_t nseg() const { return nparts; }
+    __device__ __forceinline__ int64_t m() const { return mm; }
+    __device__ __forceinline__ void range(int e, int64_t &beg, int64_t &end) const {
+        const PartDev<I, V> &pt = parts[e];
+        if (pt.ptr64) {
+            const int64_t *cp = (const int64_t *)pt.colptr;
+            beg = cp[g] - pt.sub; end = cp[g + 1] - pt.sub;
+        } else {
+            const int32_t *cp = (const int32_t *)pt.colptr;
+            beg = (int64_t)cp[g] - pt.sub; end = (int64_t)cp[g + 1] - pt.sub;
+        }
+    }
+    // entries of part e are addressed as q = e << 40 | index in the part
+    __device__ __forceinline__ void seg(int64_t e, int64_t &beg, int &len, V &bv, int64_t &tag) const {
+        int64_t b, en;
+        range((int)e, b, en);
+        beg = (e << kShift) | b; len = (int)(en - b); bv = V(1); tag = e;
+    }
+    __device__ __forceinline__ uint32_t row(int64_t q) const {
+        return (uint32_t)parts[q >> kShift].rows[q & ((1ll << kShift) - 1)];
+    }
+    __device__ __forceinline__ V val(int64_t q, V) const {
+        return parts[q >> kShift].vals[q & ((1ll << kShift) - 1)];
+    }
+    __device__ __forceinline__ int64_t flops() const {
+        const int lane = threadIdx.x & 31;
+        int64_t s = 0;
+        for (int e = lane; e < nparts; e += 32) {
+            int64_t b, en;
+            range(e, b, en);
+            s += en - b;
+        }
+        return warp_sum(s);
+    }
+};
+
+// Dense sources: contributions of column g restricted to row panel pnl;
+// lrow(q) is the row local to the panel, or -1 when outside it.
+template <class I, class V> struct SrcPanel {
+    using Args = GemmArgs<I, V>;
+    using Val = V;
+    using Idx = I;
+    const ProbDev<I, V> *p;
+    const int64_t *ape;
+    const uint16_t *apr;
+    const V *apv;
+    int64_t b0, nb, k0, k1, pk;
+    __device__ __forceinline__ void open(const Args &a, const TierCommon &, int64_t g, int pnl, int) {
+        p = a.probs;
+        const int64_t bc = g - p->gcol0;
+        b0 = (int64_t)p->bp[bc];
+        nb = (int64_t)p->bp[bc + 1] - b0;
+        k0 = a.k0; k1 = a.k1;
+        pk = (int64_t)pnl * p->ka;
+        ape = a.ap_end; apr = a.ap_row; apv = a.ap_val;
+    }
+    __device__ __forceinline__ int64_t nseg() const { return nb; }
+    __device__ __forceinline__ void seg(int64_t e, int64_t &beg, int &len, V &bv, int64_t &tag) const {
+        const int64_t pe = b0 + e;
+        const int64_t k = (int64_t)p->bi[pe];
+        if (k < k0 || k >= k1) { len = 0; return; }
+        const int64_t idx = pk + k;
+        const int64_t s = idx ? ape[idx - 1] : 0;
+        beg = s; len = (int)(ape[idx] - s); bv = p->bv[pe]; tag = pe;
+    }
+    __device__ __forceinline__ int lrow(int64_t q) const { return (int)apr[q]; }
+    __device__ __forceinline__ V val(int64_t q, V bv) const { return mul_v(apv[q], bv); }
+};
+
+template <class I, class V> struct SrcPartsPanel {
+    using Args = PartsArgs<I, V>;
+    using Val = V;
+    using Idx = I;
+    static constexpr int kShift = 40;
+    SrcParts<I, V> base;
+    int pnl, h, P;
+    int64_t r0, R;
+    __device__ __forceinline__ void open(const Args &a, const TierCommon &c, int64_t g, int pp, int hh) {
+        base.open(a, g);
+        pnl = pp; h = hh; P = c.P;
+        R = 1ll << c.log2R;
+        r0 = (int64_t)pp << c.log2R;
+    }
+    __device__ __forceinline__ int64_t nseg() const { return base.nparts; }
+    __device__ __forceinline__ void seg(int64_t e, int64_t &beg, int &len, V &bv, int64_t &tag) const {
+        int64_t b, en;
+        base.range((int)e, b, en);
+        const int32_t *pc = base.parts[e].pcnt;
+        if (pc) {   // panel-grouped column: skip the lower panels
+            const int32_t *row = pc + (int64_t)h * P;
+            int64_t off = 0;
+            for (int q = 0; q < pnl; ++q) off += row[q];
+            b += off;
+            en = b + row[pnl];
+        }
+        beg = (e << kShift) | b; len = (int)(en - b); bv = V(1); tag = e;
+    }
+    __device__ __forceinline__ int lrow(int64_t q) const {
+        const int64_t r = (int64_t)base.row(q) - r0;
+        return (r >= 0 && r < R) ? (int)r : -1;
+    }
+    __device__ __forceinline__ V val(int64_t q, V) const { return base.val(q, V(1)); }
+};
+
+// ---------------------------------------------------------------------------
+// Segment walkers. A segment is a run [beg, beg+len) of source entries
+// scaled by bv; tag names the B entry (or part) it came from.
+// emit(q, bv, tag) handles one entry.
+// ---------------------------------------------------------------------------
+
+// Warp-level: every lane holds one segment. Segments of up to short_seg
+// entries are walked by their lane; longer ones by the whole warp, one after
+// another (coalesced reads). All 32 lanes must call it.
+template <class V, class Emit>
+__device__ __forceinline__ void warp_walk(int64_t beg, int len, V bv, int64_t tag, int short_seg,
+                                          Emit &emit) {
+    const int lane = threadIdx.x & 31;
+    unsigned longmask = __ballot_sync(SPG_FULL, len > short_seg);
+    if (len <= short_seg) {
+        for (int i = 0; i < len; ++i) emit(beg + i, bv, tag);
+    }
+    while (longmask) {
+        const int src = __ffs(longmask) - 1;
+        longmask &= longmask - 1;
+        const int64_t b = __shfl_sync(SPG_FULL, beg, src);
+        const int l = __shfl_sync(SPG_FULL, len, src);
+        const V v = __shfl_sync(SPG_FULL, bv, src);
+        const int64_t tg = __shfl_sync(SPG_FULL, tag, src);
+        for (int i = lane; i < l; i += 32) emit(b + i, v, tg);
+    }
+}
+
+template <class V> struct HugeSeg { int64_t beg; int64_t tag; V bv; int len; };
+
+constexpr int kHugeQ = 32;
+
+template <class V> struct BlockShared {
+    HugeSeg<V> hq[kHugeQ];
+    int hq_n;
+    int pos;
+    unsigned long long tot;
+    int red[32];
+};
+
+// Block-level walk over the segments of src. Segments longer than huge_seg
+// are queued and walked by the whole CTA. All threads must call it; it ends
+// with a __syncthreads.
+template <class Src, class Emit>
+__device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short_seg, int huge_seg,
+                                           BlockShared<typename Src::Val> &sh) {
+    using V = typename Src::Val;
+    const int64_t nseg = src.nseg();
+    for (int64_t base = 0; base < nseg; base += blockDim.x) {
+        const int64_t e = base + threadIdx.x;
+        int64_t beg = 0, tag = 0;
+        int len = 0;
+        V bv = V(0);
+        if (e < nseg) src.seg(e, beg, len, bv, tag);
+        if (len > huge_seg) {
+            const int slot = atomicAdd(&sh.hq_n, 1);
+            if (slot < kHugeQ) {
+                sh.hq[slot].beg = beg; sh.hq[slot].len = len; sh.hq[slot].bv = bv;
+                sh.hq[slot].tag = tag;
+                len = 0;
+            }
+        }
+        warp_walk(beg, len, bv, tag, short_seg, emit);
+        __syncthreads();
+        int nh = sh.hq_n;
+        if (nh > kHugeQ) nh = kHugeQ;
+        for (int h = 0; h < nh; ++h) {
+            const HugeSeg<V> s = sh.hq[h];
+            for (int i = threadIdx.x; i < s.len; i += blockDim.x) emit(s.beg + i, s.bv, s.tag);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) sh.hq_n = 0;
+        __syncthreads();
+    }
+}
+
+// Warp walk over all segments of src (one warp per column).
+template <class Src, class Emit>
+__device__ __forceinline__ void warp_walk_all(const Src &src, Emit &emit, int short_seg) {
+    using V = typename Src::Val;
+    const int lane = threadIdx.x & 31;
+    const int64_t nb = src.nseg();
+    for (int64_t base = 0; base < nb; base += 32) {
+        int64_t beg = 0, tag = 0;
+        int len = 0;
+        V bv = V(0);
+        if (base + lane < nb) src.seg(base + lane, beg, len, bv, tag);
+        warp_walk(beg, len, bv, tag, short_seg, emit);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory hash tables (linear probing, 32-bit keys)
+// ---------------------------------------------------------------------------
+
+// Insert key; returns its slot and sets is_new when this call claimed it.
+// Returns -1 (and records kErrProbe) if the table is full -- impossible when
+// the table has more slots than the column has distinct rows.
+__device__ __forceinline__ int hash_insert(uint32_t *keys, int log2T, uint32_t key, bool &is_new,
+                                           int *err) {
+    const uint32_t mask = (1u << log2T) - 1u;
+    uint32_t h = hash_slot(key, log2T);
+    is_new = false;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint32_t cur = keys[h];
+        if (cur == key) return (int)h;
+        if (cur == kEmpty) {
+            const uint32_t old = atomicCAS(&keys[h], kEmpty, key);
+            if (old == kEmpty) { is_new = true; return (int)h; }
+            if (old == key) return (int)h;
+        }
+        h = (h + 1) & mask;
+    }
+    atomicOr(err, kErrProbe);
+    return -1;
+}
+
+// Lookup only; -1 when absent.
+__device__ __forceinline__ int hash_find(const uint32_t *keys, int log2T, uint32_t key) {
+    const uint32_t mask = (1u << log2T) - 1u;
+    uint32_t h = hash_slot(key, log2T);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint32_t cur = keys[h];
+        if (cur == key) return (int)h;
+        if (cur == kEmpty) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+template <int T> struct Log2 { static constexpr int v = 1 + Log2<T / 2>::v; };
+template <> struct Log2<1> { static constexpr int v = 0; };
+
+// ---------------------------------------------------------------------------
+// K1: contributions per column (flops for a product) and tier binning
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int heavy_subtier(int64_t u) {
+    const int lg = 63 - __clzll((unsigned long long)(u | 1));
+    const int h = kHeavyTier0 + (lg - 13 < 0 ? 0 : lg - 13);
+    return h > kTiers - 1 ? kTiers - 1 : h;
+}
+
+__device__ __forceinline__ int hash_tier_of(int64_t u, int hash_cap_max) {
+    if (u == 0) return 0;
+    for (int t = 1; t <= 8; ++t) {
+        const int cap = tier_cap(t);
+        if (cap > hash_cap_max) break;
+        if (u <= cap) return t;
+    }
+    return -1;
+}
+
+// One warp per column computes f_j, the number of contributions; the CTA
+// keeps a tier histogram. bound (optional) is the exact count of the unsplit
+// product when a k-stage is binned: columns with bound > hash_cap_max go to
+// the heavy tier (their stage output must be panel-grouped), others use
+// min(f, bound) as their size.
+template <class Src>
+__global__ void __launch_bounds__(256) k_flops_bin(typename Src::Args sa, int64_t c_lo,
+                                                   int64_t c_hi, int hash_cap_max,
+                                                   const int64_t *bound, int64_t *f_out,
+                                                   uint8_t *tier_out, int64_t *cnt_out,
+                                                   int32_t *tier_hist) {
+    __shared__ int s_hist[kTiers];
+    if (threadIdx.x < kTiers) s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t cbase = c_lo + (int64_t)blockIdx.x * 256;
+    for (int c = 0; c < 32; ++c) {
+        const int64_t g = cbase + warp * 32 + c;
+        if (g >= c_hi) break;
+        Src src;
+        src.open(sa, g);
+        const int64_t f = src.flops();
+        if (lane == 0) {
+            int64_t u = f < src.m() ? f : src.m();
+            int t;
+            if (bound && bound[g] > hash_cap_max) {
+                t = heavy_subtier(f);
+            } else {
+                if (bound && bound[g] < u) u = bound[g];
+                t = hash_tier_of(u, hash_cap_max);
+                if (t < 0) t = heavy_subtier(u);
+            }
+            if (f_out) f_out[g] = f;
+            tier_out[g] = (uint8_t)t;
+            if (cnt_out) cnt_out[g] = 0;
+            if (t) atomicAdd(&s_hist[t], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kTiers && s_hist[threadIdx.x])
+        atomicAdd(&tier_hist[threadIdx.x], s_hist[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// K2: symbolic hash tiers (count distinct rows per column)
+// ---------------------------------------------------------------------------
+template <class Src, int T>
+__global__ void __launch_bounds__(256) k_sym_warp(typename Src::Args sa, TierCommon c) {
+    constexpr int LOG2T = Log2<T>::v;
+    using V = typename Src::Val;
+    __shared__ uint32_t s_keys[8][T];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *keys = s_keys[warp];
+    const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
+    const int nwarps = gridDim.x * 8;
+    for (int it = lo + blockIdx.x * 8 + warp; it < hi; it += nwarps) {
+        const int64_t g = c.list[it];
+        Src src;
+        src.open(sa, g);
+        for (int s = lane; s < T; s += 32) keys[s] = kEmpty;
+        __syncwarp();
+        int mine = 0;
+        auto emit = [&](int64_t q, V, int64_t) {
+            bool nw;
+            hash_insert(keys, LOG2T, src.row(q), nw, c.err);
+            mine += nw;
+        };
+        warp_walk_all(src, emit, c.short_seg);
+        mine = warp_sum(mine);
+        if (lane == 0) c.cnt[g] = mine;
+        __syncwarp();
+    }
+}
+
+template <class Src, int T>
+__global__ void k_sym_block(typename Src::Args sa, TierCommon c) {
+    constexpr int LOG2T = Log2<T>::v;
+    using V = typename Src::Val;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *keys = reinterpret_cast<uint32_t *>(smem);
+    __shared__ BlockShared<V> sh;
+    if (threadIdx.x == 0) sh.hq_n = 0;
+    const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
+    for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {
+        const int64_t g = c.list[it];
+        Src src;
+        src.open(sa, g);
+        for (int s = threadIdx.x; s < T; s += blockDim.x) keys[s] = kEmpty;
+        __syncthreads();
+        int mine = 0;
+        auto emit = [&](int64_t q, V, int64_t) {
+            bool nw;
+            hash_insert(keys, LOG2T, src.row(q), nw, c.err);
+            mine += nw;
+        };
+        block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+        mine = warp_sum(mine);
+        if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = mine;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int v = threadIdx.x < (int)(blockDim.x >> 5) ? sh.red[threadIdx.x] : 0;
+            v = warp_sum(v);
+            if (threadIdx.x == 0) c.cnt[g] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Heavy symbolic: a shared-memory bitmap over Rs rows. Items are (symbolic
+// panel q, heavy column), largest heavy sub-tier first. Writes per numeric
+// panel counts pcnt[h*P + p] and adds the column total to cnt[g].
+template <class Src>
+__global__ void __launch_bounds__(1024) k_sym_bitmap(typename Src::Args sa, TierCommon c) {
+    using V = typename Src::Val;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *bm = reinterpret_cast<uint32_t *>(smem);
+    __shared__ BlockShared<V> sh;
+    const int nwords_max = (int)((c.Rs + 31) >> 5);
+    for (int w = threadIdx.x; w < nwords_max; w += blockDim.x) bm[w] = 0u;
+    if (threadIdx.x == 0) { sh.hq_n = 0; sh.tot = 0; }
+    __syncthreads();
+    const int lo = c.list_off[kHeavyTier0], hi = c.list_off[kTiers];
+    const int64_t nitems = (int64_t)(hi - lo) * c.Q;
+    const int wordsR = 1 << (c.log2R - 5);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int64_t ri = nitems - 1 - item;   // list is ascending in sub-tier
+        const int hpos = (int)(ri / c.Q);
+        const int q = (int)(ri % c.Q);
+        const int64_t g = c.list[lo + hpos];
+        Src src;
+        src.open(sa, g);
+        const int64_t r0 = (int64_t)q * c.Rs;
+        const int64_t mrows = src.m();
+        const int64_t rows = (mrows - r0) < c.Rs ? (mrows - r0) : c.Rs;
+        const int nwords = (int)((rows + 31) >> 5);
+        const bool filt = c.Q > 1;
+        auto emit = [&](int64_t qq, V, int64_t) {
+            int64_t r = (int64_t)src.row(qq);
+            if (filt) {
+                r -= r0;
+                if (r < 0 || r >= rows) return;
+            }
+            atomicOr(&bm[r >> 5], 1u << (r & 31));
+        };
+        block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+        const int h = c.heavy_ord[g];
+        const int p0 = (int)(r0 >> c.log2R);
+        const int np = (nwords + wordsR - 1) / wordsR;
+        for (int pp = warp; pp < np; pp += nw) {
+            const int w0 = pp * wordsR;
+            const int w1 = (w0 + wordsR) < nwords ? (w0 + wordsR) : nwords;
+            int cntp = 0;
+            for (int w = w0 + lane; w < w1; w += 32) { cntp += __popc(bm[w]); bm[w] = 0u; }
+            cntp = warp_sum(cntp);
+            if (lane == 0) {
+                c.pcnt[(int64_t)h * c.P + p0 + pp] = cntp;
+                if (cntp) atomicAdd(&sh.tot, (unsigned long long)cntp);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (c.Q == 1) c.cnt[g] = (int64_t)sh.tot;
+            else atomicAdd(reinterpret_cast<unsigned long long *>(&c.cnt[g]), sh.tot);
+            sh.tot = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K3 / K4: numeric hash tiers (products or merge), unsorted output
+// ---------------------------------------------------------------------------
+template <class Src, int T>
+__global__ void __launch_bounds__(256) k_num_warp(typename Src::Args sa, TierCommon c,
+                                                  typename Src::Idx *out_rows,
+                                                  typename Src::Val *out_vals) {
+    constexpr int LOG2T = Log2<T>::v;
+    using V = typename Src::Val;
+    using I = typename Src::Idx;
+    __shared__ uint32_t s_keys[8][T];
+    __shared__ V s_vals[8][T];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *keys = s_keys[warp];
+    V *vals = s_vals[warp];
+    const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
+    const int nwarps = gridDim.x * 8;
+    for (int it = lo + blockIdx.x * 8 + warp; it < hi; it += nwarps) {
+        const int64_t g = c.list[it];
+        Src src;
+        src.open(sa, g);
+        for (int s = lane; s < T; s += 32) { keys[s] = kEmpty; vals[s] = V(0); }
+        __syncwarp();
+        auto emit = [&](int64_t q, V bv, int64_t) {
+            bool nw;
+            const int h = hash_insert(keys, LOG2T, src.row(q), nw, c.err);
+            if (h >= 0) atomic_add_v(&vals[h], src.val(q, bv));
+        };
+        warp_walk_all(src, emit, c.short_seg);
+        __syncwarp();
+        const int64_t out0 = c.colptr[g] - c.out_base;
+        const int64_t want = c.colptr[g + 1] - c.colptr[g];
+        int pos = 0;
+        for (int s0 = 0; s0 < T; s0 += 32) {
+            const int s = s0 + lane;
+            const uint32_t key = keys[s];
+            const bool occ = key != kEmpty;
+            const unsigned bal = __ballot_sync(SPG_FULL, occ);
+            if (occ) {
+                const int r = pos + __popc(bal & ((1u << lane) - 1u));
+                if (r < want) {
+                    out_rows[out0 + r] = (I)key;
+                    out_vals[out0 + r] = vals[s];
+                }
+            }
+            pos += __popc(bal);
+        }
+        if (lane == 0 && pos != want) atomicOr(c.err, kErrCount);
+        __syncwarp();
+    }
+}
+
+template <class Src, int T>
+__global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::Idx *out_rows,
+                            typename Src::Val *out_vals) {
+    constexpr int LOG2T = Log2<T>::v;
+    using V = typename Src::Val;
+    using I = typename Src::Idx;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V *vals = reinterpret_cast<V *>(smem);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * T);
+    __shared__ BlockShared<V> sh;
+    if (threadIdx.x == 0) { sh.hq_n = 0; sh.pos = 0; }
+    const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
+    const int lane = threadIdx.x & 31;
+    for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {
+        const int64_t g = c.list[it];
+        Src src;
+        src.open(sa, g);
+        for (int s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = kEmpty; vals[s] = V(0); }
+        __syncthreads();
+        auto emit = [&](int64_t q, V bv, int64_t) {
+            bool nw;
+            const int h = hash_insert(keys, LOG2T, src.row(q), nw, c.err);
+            if (h >= 0) atomic_add_v(&vals[h], src.val(q, bv));
+        };
+        block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+        const int64_t out0 = c.colptr[g] - c.out_base;
+        const int64_t want = c.colptr[g + 1] - c.colptr[g];
+        for (int s0 = 0; s0 < T; s0 += blockDim.x) {
+            const int s = s0 + threadIdx.x;
+            const uint32_t key = s < T ? keys[s] : kEmpty;
+            const bool occ = key != kEmpty;
+            const unsigned bal = __ballot_sync(SPG_FULL, occ);
+            int wbase = 0;
+            if (lane == 0 && bal) wbase = atomicAdd(&sh.pos, __popc(bal));
+            wbase = __shfl_sync(SPG_FULL, wbase, 0);
+            if (occ) {
+                const int r = wbase + __popc(bal & ((1u << lane) - 1u));
+                if (r < want) {
+                    out_rows[out0 + r] = (I)key;
+                    out_vals[out0 + r] = vals[s];
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (sh.pos != want) atomicOr(c.err, kErrCount);
+            sh.pos = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// Heavy numeric: dense accumulation of one row panel of one column in shared
+// memory (values + a presence bitmap). Items (p, h) are panel-major so that
+// the CTAs running at the same time share one panel of A in L2. An item writes
+// pcnt_in[h*P+p] entries at the column's offset plus the counts of the lower
+// panels (rows grouped by panel, ascending within the panel).
+template <class DSrc>
+__global__ void __launch_bounds__(1024) k_num_dense(typename DSrc::Args sa, TierCommon c,
+                                                    typename DSrc::Idx *out_rows,
+                                                    typename DSrc::Val *out_vals) {
+    using V = typename DSrc::Val;
+    using I = typename DSrc::Idx;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int R = 1 << c.log2R;
+    V *acc = reinterpret_cast<V *>(smem);
+    uint32_t *bm = reinterpret_cast<uint32_t *>(smem + sizeof(V) * R);
+    __shared__ BlockShared<V> sh;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) acc[r] = V(0);
+    for (int w = threadIdx.x; w < (R >> 5); w += blockDim.x) bm[w] = 0u;
+    if (threadIdx.x == 0) { sh.hq_n = 0; sh.pos = 0; }
+    __syncthreads();
+    const int lo = c.list_off[kHeavyTier0], hi = c.list_off[kTiers];
+    const int nh = hi - lo;
+    const int64_t nitems = (int64_t)nh * c.P;
+    const int lane = threadIdx.x & 31;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int p = (int)(item / nh);
+        const int hl = (int)(item % nh);
+        const int64_t g = c.list[lo + hl];
+        if (g < c.c_lo || g >= c.c_hi) continue;
+        if (c.dense_sel[g] <= c.hash_cap_max) continue;   // a hash tier has it
+        const int h = c.heavy_ord[g];
+        const int32_t *pc = c.pcnt_in + (int64_t)h * c.P;
+        const int mycnt = pc[p];
+        if (mycnt == 0) continue;
+        int below = 0;
+        for (int pp = lane; pp < p; pp += 32) below += pc[pp];
+        below = warp_sum(below);
+        const int64_t out0 = c.colptr[g] - c.out_base + below;
+        DSrc src;
+        src.open(sa, c, g, p, h);
+        auto emit = [&](int64_t q, V bv, int64_t) {
+            const int r = src.lrow(q);
+            if (r < 0) return;
+            atomic_add_v(&acc[r], src.val(q, bv));
+            atomicOr(&bm[r >> 5], 1u << (r & 31));
+        };
+        block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+        // compaction: each thread takes bitmap words; warp-aggregated slots
+        const int64_t rbase = (int64_t)p << c.log2R;
+        for (int w0 = 0; w0 < (R >> 5); w0 += blockDim.x) {
+            const int w = w0 + threadIdx.x;
+            uint32_t x = w < (R >> 5) ? bm[w] : 0u;
+            const int n1 = __popc(x);
+            const int incl = warp_incl_scan(n1);
+            const int tot = __shfl_sync(SPG_FULL, incl, 31);
+            int wb = 0;
+            if (lane == 31 && tot) wb = atomicAdd(&sh.pos, tot);
+            wb = __shfl_sync(SPG_FULL, wb, 31);
+            if (x) {
+                bm[w] = 0u;
+                int o = wb + incl - n1;
+                while (x) {
+                    const int bit = __ffs(x) - 1;
+                    x &= x - 1;
+                    const int r = w * 32 + bit;
+                    if (o < mycnt) {
+                        out_rows[out0 + o] = (I)(rbase + r);
+                        out_vals[out0 + o] = acc[r];
+                    }
+                    acc[r] = V(0);
+                    ++o;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (sh.pos != mycnt) atomicOr(c.err, kErrCount);
+            sh.pos = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row panels of A for the dense numeric tier
+// ---------------------------------------------------------------------------
+
+// count[p*ka + c] += entries of A(:, c) in row panel p (one warp per column).
+template <class I>
+__global__ void k_panel_count(const I *ap, const I *ai, int64_t ka, int log2R,
+                              unsigned long long *count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t col = wid; col < ka; col += nw) {
+        const int64_t a0 = (int64_t)ap[col], a1 = (int64_t)ap[col + 1];
+        for (int64_t q = a0 + lane; q < a1; q += 32) {
+            const int64_t p = (int64_t)ai[q] >> log2R;
+            atomicAdd(&count[p * ka + col], 1ull);
+        }
+    }
+}
+
+// cursor[idx] starts at the segment start (exclusive scan of the counts);
+// every entry takes a slot with atomicAdd, which leaves cursor[idx] at the
+// segment end.
+template <class I, class V>
+__global__ void k_panel_scatter(const I *ap, const I *ai, const V *av, int64_t ka, int log2R,
+                                unsigned long long *cursor, uint16_t *out_row, V *out_val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t mask = (1ll << log2R) - 1;
+    for (int64_t col = wid; col < ka; col += nw) {
+        const int64_t a0 = (int64_t)ap[col], a1 = (int64_t)ap[col + 1];
+        for (int64_t q = a0 + lane; q < a1; q += 32) {
+            const int64_t r = (int64_t)ai[q];
+            const int64_t p = r >> log2R;
+            const unsigned long long pos = atomicAdd(&cursor[p * ka + col], 1ull);
+            out_row[pos] = (uint16_t)(r & mask);
+            out_val[pos] = av[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: masked-SpGEMM backward. For every product A(i,k) B(k,j) of column j:
+//   dA(i,k) += G(i,j) B(k,j),  dB(k,j) += A(i,k) G(i,j),
+// with G(:,j) loaded into a shared-memory hash table (key row -> value).
+// Columns are tiered by nnz(G(:,j)); columns above the largest table use a
+// dense per-panel copy of G(:,j), one item per (panel, column), filtering
+// the products by row.
+// ---------------------------------------------------------------------------
+template <class I, class V> struct GradArgs {
+    GemmArgs<I, V> gemm;
+    const void *gcolptr;
+    int gptr64;
+    const I *grows;
+    const V *gvals;
+    V *dA;
+    V *dB;
+};
+
+template <class I, class V>
+__device__ __forceinline__ void g_range(const GradArgs<I, V> &a, int64_t g, int64_t &b, int64_t &e) {
+    if (a.gptr64) {
+        b = ((const int64_t *)a.gcolptr)[g]; e = ((const int64_t *)a.gcolptr)[g + 1];
+    } else {
+        b = ((const int32_t *)a.gcolptr)[g]; e = ((const int32_t *)a.gcolptr)[g + 1];
+    }
+}
+
+template <class I, class V, int T>
+__global__ void k_bwd_block(GradArgs<I, V> a, TierCommon c) {
+    constexpr int LOG2T = Log2<T>::v;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V *gv = reinterpret_cast<V *>(smem);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * T);
+    __shared__ BlockShared<V> sh;
+    if (threadIdx.x == 0) sh.hq_n = 0;
+    const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
+    for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {
+        const int64_t g = c.list[it];
+        for (int s = threadIdx.x; s < T; s += blockDim.x) keys[s] = kEmpty;
+        __syncthreads();
+        int64_t gb, ge;
+        g_range(a, g, gb, ge);
+        for (int64_t q = gb + threadIdx.x; q < ge; q += blockDim.x) {
+            bool nw;
+            const int h = hash_insert(keys, LOG2T, (uint32_t)a.grows[q], nw, c.err);
+            if (h >= 0) gv[h] = a.gvals[q];
+        }
+        __syncthreads();
+        SrcGemm<I, V> src;
+        src.open(a.gemm, g);
+        auto emit = [&](int64_t q, V bv, int64_t pe) {
+            const int h = hash_find(keys, LOG2T, src.row(q));
+            if (h < 0) return;
+            const V gval = gv[h];
+            atomic_add_v(&a.dA[q], mul_v(gval, bv));
+            atomic_add_v(&a.dB[pe], mul_v(src.p->av[q], gval));
+        };
+        block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+    }
+}
+
+template <class I, class V, int T>
+__global__ void __launch_bounds__(256) k_bwd_warp(GradArgs<I, V> a, TierCommon c) {
+    constexpr int LOG2T = Log2<T>::v;
+    __shared__ uint32_t s_keys[8][T];
+    __shared__ V s_vals[8][T];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *keys = s_keys[warp];
+    V *gv = s_vals[warp];
+    const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
+    const int nwarps = gridDim.x * 8;
+    for (int it = lo + blockIdx.x * 8 + warp; it < hi; it += nwarps) {
+        const int64_t g = c.list[it];
+        for (int s = lane; s < T; s += 32) keys[s] = kEmpty;
+        __syncwarp();
+        int64_t gb, ge;
+        g_range(a, g, gb, ge);
+        for (int64_t q = gb + lane; q < ge; q += 32) {
+            bool nw;
+            const int h = hash_insert(keys, LOG2T, (uint32_t)a.grows[q], nw, c.err);
+            if (h >= 0) gv[h] = a.gvals[q];
+        }
+        __syncwarp();
+        SrcGemm<I, V> src;
+        src.open(a.gemm, g);
+        auto emit = [&](int64_t q, V bv, int64_t pe) {
+            const int h = hash_find(keys, LOG2T, src.row(q));
+            if (h < 0) return;
+            const V gval = gv[h];
+            atomic_add_v(&a.dA[q], mul_v(gval, bv));
+            atomic_add_v(&a.dB[pe], mul_v(src.p->av[q], gval));
+        };
+        warp_walk_all(src, emit, c.short_seg);
+        __syncwarp();
+    }
+}
+
+// Heavy backward: dense panel of G(:,j) in shared memory; the products of the
+// column are filtered to the panel's rows. Items (p, column) over the heavy
+// list; an item with no G entries in its panel is skipped.
+template <class I, class V>
+__global__ void __launch_bounds__(1024) k_bwd_dense(GradArgs<I, V> a, TierCommon c) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int R = 1 << c.log2R;
+    V *gd = reinterpret_cast<V *>(smem);
+    uint32_t *bm = reinterpret_cast<uint32_t *>(smem + sizeof(V) * R);
+    __shared__ BlockShared<V> sh;
+    __shared__ int s_any;
+    for (int w = threadIdx.x; w < (R >> 5); w += blockDim.x) bm[w] = 0u;
+    if (threadIdx.x == 0) { sh.hq_n = 0; s_any = 0; }
+    __syncthreads();
+    const int lo = c.list_off[kHeavyTier0], hi = c.list_off[kTiers];
+    const int nh = hi - lo;
+    const int64_t nitems = (int64_t)nh * c.P;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int p = (int)(item / nh);
+        const int64_t g = c.list[lo + (int)(item % nh)];
+        const int64_t r0 = (int64_t)p << c.log2R;
+        int64_t gb, ge;
+        g_range(a, g, gb, ge);
+        for (int64_t q = gb + threadIdx.x; q < ge; q += blockDim.x) {
+            const int64_t r = (int64_t)a.grows[q] - r0;
+            if (r >= 0 && r < R) {
+                gd[r] = a.gvals[q];
+                atomicOr(&bm[r >> 5], 1u << (r & 31));
+                s_any = 1;
+            }
+        }
+        __syncthreads();
+        if (s_any) {
+            SrcGemm<I, V> src;
+            src.open(a.gemm, g);
+            auto emit = [&](int64_t q, V bv, int64_t pe) {
+                const int64_t r = (int64_t)src.row(q) - r0;
+                if (r < 0 || r >= R) return;
+                if (!((bm[r >> 5] >> (r & 31)) & 1u)) return;
+                const V gval = gd[r];
+                atomic_add_v(&a.dA[q], mul_v(gval, bv));
+                atomic_add_v(&a.dB[pe], mul_v(src.p->av[q], gval));
+            };
+            block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+        }
+        for (int w = threadIdx.x; w < (R >> 5); w += blockDim.x) bm[w] = 0u;
+        __syncthreads();
+        if (threadIdx.x == 0) s_any = 0;
+        __syncthreads();
+    }
+}
+
+// Tiering of the backward columns by nnz(G(:, j)).
+template <class I, class V>
+__global__ void k_bwd_tier(GradArgs<I, V> a, int64_t n, int hash_cap_max, uint8_t *tier_out,
+                           int32_t *tier_hist) {
+    __shared__ int s_hist[kTiers];
+    if (threadIdx.x < kTiers) s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) {
+        int64_t b, e;
+        g_range(a, g, b, e);
+        const int64_t cnt = e - b;
+        int t = hash_tier_of(cnt, hash_cap_max);
+        if (t < 0) t = kHeavyTier0;
+        if (cnt == 0) t = 0;
+        tier_out[g] = (uint8_t)t;
+        if (t) atomicAdd(&s_hist[t], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kTiers && s_hist[threadIdx.x])
+        atomicAdd(&tier_hist[threadIdx.x], s_hist[threadIdx.x]);
+}
+
+template <class V> __global__ void k_fill_zero(V *p, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = V(0);
+}
+
+}  // namespace spg

@@ -1,0 +1,155 @@
+// Plan state shared by the C ABI and the typed engines.
+#pragma once
+
+#include <cstdint>
+#include <array>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/spgemm.h"
+
+namespace spg {
+
+// A grow-only device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t want) {
+        if (want <= bytes && p) return cudaSuccess;
+        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+        if (want == 0) want = 16;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) bytes = want; else p = nullptr;
+        return e;
+    }
+    void release() { if (p) cudaFree(p); p = nullptr; bytes = 0; }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// A grow-only pinned host buffer.
+struct HostBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t want) {
+        if (want <= bytes && p) return cudaSuccess;
+        if (p) { cudaFreeHost(p); p = nullptr; bytes = 0; }
+        if (want == 0) want = 16;
+        cudaError_t e = cudaHostAlloc(&p, want, cudaHostAllocDefault);
+        if (e == cudaSuccess) bytes = want; else p = nullptr;
+        return e;
+    }
+    void release() { if (p) cudaFreeHost(p); p = nullptr; bytes = 0; }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct Tuning {
+    int hash_cap_max = 8192;
+    int log2R = 15;          // dense panel rows (set per value type at plan time)
+    int short_seg = 8;
+    int huge_seg = 4096;
+    int block_threads = 0;   // 0: per-tier default
+};
+
+struct Batch {
+    int64_t c0 = 0, c1 = 0;  // column range
+    int64_t nnz = 0;         // nnz(C) of the batch
+    int64_t unmerged = 0;    // sum over stages of nnz(D_t) of the batch (s > 1)
+    // numeric hash-tier populations: [0] the product (s = 1) or the merge,
+    // [1 + t] stage t (s > 1); host copies computed from the counts
+    std::vector<std::array<int, 16>> tc;
+    int64_t heavy = 0;       // columns above the largest hash table
+    std::vector<int64_t> doff;  // offset of stage t's partials in the partial buffer
+};
+
+struct EngineBase;
+
+struct PlanState {
+    spgemm_csc A{}, B{};
+    spgemm_opts opts{};
+    Tuning tun;
+    int idx64 = 0, vtype = 0;
+    int64_t m = 0, k = 0, n = 0;
+    int s = 1;
+    size_t budget = 0;
+    int dev = 0, nsm = 148;
+    EngineBase *eng = nullptr;
+
+    // device workspace
+    DevBuf probs, f, cnt, colptr, tier, list_sym, list_num, hist, cursor, off_sym, off_num;
+    DevBuf heavy_ord, pcnt, err, scan_part, wbytes, valid_flag;
+    DevBuf ap_end, ap_row, ap_val;
+    DevBuf stage_cnt, stage_colptr, stage_pcnt, drows, dvals, parts_tab;  // k-split
+    DevBuf merge_tmp;
+    HostBuf h_colptr, h_small, h_stage_colptr, h_parts;
+    std::vector<DevBuf> ring_col, ring_row, ring_val;   // spgemm_run_batched device ring
+    std::vector<HostBuf> host_slots;                     // spgemm_run_batched pinned slots
+
+    // symbolic results
+    bool have_symbolic = false;
+    int64_t flops = 0, nnz_c = 0, unmerged = 0;
+    int sym_hist[16] = {0};
+    int nheavy = 0;          // symbolic heavy columns (dense path candidates)
+    int P = 0, Q = 0;        // numeric panels, symbolic panels
+    int64_t Rs = 0;          // symbolic bitmap rows
+    bool panels_built = false;
+    std::vector<Batch> batches;
+    int64_t batch_cap = 0;
+    int64_t bytes_per_nnz = 0;
+
+    size_t workspace_bytes() const;
+    void release_all();
+};
+
+// Typed engine: one per (index, value) type pair.
+struct EngineBase {
+    virtual ~EngineBase() {}
+    virtual spgemm_status setup(PlanState &ps, cudaStream_t st) = 0;
+    virtual spgemm_status symbolic(PlanState &ps, cudaStream_t st) = 0;
+    virtual spgemm_status numeric(PlanState &ps, int64_t t, spgemm_csc *C, cudaStream_t st) = 0;
+    virtual spgemm_status backward(PlanState &ps, const spgemm_csc *G, void *dA, void *dB,
+                                   cudaStream_t st) = 0;
+};
+
+// Type-erased standalone merge (spgemm_merge).
+spgemm_status merge_dispatch(const spgemm_csc *parts, int nparts, spgemm_csc *out,
+                             cudaStream_t st);
+
+EngineBase *make_engine(int idx64, int vtype);
+
+// thread-local error message
+void set_error(const std::string &msg);
+spgemm_status cuda_fail(cudaError_t e, const char *where);
+
+}  // namespace spg
+
+struct spgemm_plan_s {
+    spg::PlanState ps;
+};
+
+namespace spg {
+
+// State of a multi-problem run (spgemm_multi).
+struct MultiState {
+    int nprob = 0, idx64 = 0, vtype = 0, nsm = 148;
+    Tuning tun;
+    DevBuf probs, f, cnt, colptr, tier, list, off, list2, off2, hist, cursor, err, scan_part;
+    DevBuf rows, vals;
+    HostBuf h_small;
+    int64_t total_cols = 0, capacity = 0, total_flops = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t own = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    spgemm_status (*enqueue)(MultiState &, cudaStream_t) = nullptr;
+    void release_all();
+};
+
+spgemm_status multi_create_typed(MultiState &ms, const spgemm_csc *As, const spgemm_csc *Bs,
+                                 cudaStream_t st);
+
+}  // namespace spg
+
+struct spgemm_multi_s {
+    spg::MultiState ms;
+};

@@ -1,0 +1,230 @@
+// Non-templated helper kernels: numeric tiering, tier scatter, int64 scans,
+// small copies.
+#include "util.h"
+#include "kernels.cuh"
+
+namespace spg {
+
+__device__ __forceinline__ int num_tier_of(int64_t n, int hash_cap_max) {
+    if (n == 0) return 0;
+    for (int t = 1; t <= 8; ++t) {
+        const int cap = tier_cap(t);
+        if (cap > hash_cap_max) break;
+        if (n <= cap) return t;
+    }
+    return kHeavyTier0;
+}
+
+__global__ void k_numeric_tier(const int64_t *cnt, const int64_t *dense_sel, int64_t c_lo,
+                               int64_t c_hi, int hash_cap_max, uint8_t *tier_out,
+                               int32_t *tier_hist) {
+    __shared__ int s_hist[kTiers];
+    if (threadIdx.x < kTiers) s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t g = c_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < c_hi) {
+        int t = num_tier_of(cnt[g], hash_cap_max);
+        if (dense_sel && dense_sel[g] > hash_cap_max) t = kHeavyTier0;
+        tier_out[g] = (uint8_t)t;
+        if (t) atomicAdd(&s_hist[t], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kTiers && s_hist[threadIdx.x]) atomicAdd(&tier_hist[threadIdx.x], s_hist[threadIdx.x]);
+}
+
+__global__ void k_bin_scatter(const uint8_t *tier, int64_t c_lo, int64_t c_hi,
+                              const int32_t *tier_hist, int32_t *cursor, int32_t *list,
+                              int32_t *list_off, int32_t *heavy_ord) {
+    __shared__ int s_off[kTiers + 1];
+    __shared__ int s_cnt[kTiers];
+    __shared__ int s_base[kTiers];
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int t = 0; t < kTiers; ++t) { s_off[t] = acc; acc += (t == 0 ? 0 : tier_hist[t]); }
+        s_off[kTiers] = acc;
+        if (blockIdx.x == 0)
+            for (int t = 0; t <= kTiers; ++t) list_off[t] = s_off[t];
+    }
+    if (threadIdx.x < kTiers) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t g = c_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int t = 0, rank = 0;
+    if (g < c_hi) {
+        t = tier[g];
+        if (t) rank = atomicAdd(&s_cnt[t], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kTiers && s_cnt[threadIdx.x])
+        s_base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], s_cnt[threadIdx.x]);
+    __syncthreads();
+    if (g < c_hi && t) {
+        const int pos = s_off[t] + s_base[t] + rank;
+        list[pos] = (int32_t)g;
+        if (heavy_ord && t >= kHeavyTier0) heavy_ord[g] = pos - s_off[kHeavyTier0];
+    }
+}
+
+// ---- exclusive scan of int64 (three phases, all on the device) ------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *s_warp, int64_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t incl = warp_incl_scan(v);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+        int64_t wi = warp_incl_scan(w);
+        s_warp[lane] = wi - w;
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    int64_t r = s_warp[warp] + incl - v;
+    total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int64_t *in, int64_t n,
+                                                              int64_t *partials) {
+    __shared__ int64_t s_warp[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
+        if (idx < n) s += in[idx];
+    }
+    int64_t total;
+    block_excl_scan(s, s_warp, total);
+    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(int64_t *partials, int64_t np) {
+    __shared__ int64_t s_warp[33];
+    int64_t carry = 0;
+    for (int64_t b = 0; b < np; b += kScanThreads) {
+        const int64_t i = b + threadIdx.x;
+        int64_t v = i < np ? partials[i] : 0;
+        int64_t total;
+        int64_t ex = block_excl_scan(v, s_warp, total);
+        if (i < np) partials[i] = ex + carry;
+        carry += total;
+    }
+    if (threadIdx.x == 0) partials[np] = carry;
+}
+
+// out[i] = sum_{j<i} in[j] for i in [0, n]; in and out may alias.
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int64_t *in, int64_t n,
+                                                             const int64_t *partials,
+                                                             int64_t *out, int write_total) {
+    __shared__ int64_t s_warp[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t idx = base + i;
+        v[i] = idx < n ? in[idx] : 0;
+        s += v[i];
+    }
+    int64_t total;
+    int64_t ex = block_excl_scan(s, s_warp, total) + partials[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t idx = base + i;
+        if (idx < n) out[idx] = ex;
+        ex += v[i];
+    }
+    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+        out[n] = partials[gridDim.x];
+}
+
+int64_t scan_partials_len(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t exclusive_scan_i64(const int64_t *in, int64_t n, int64_t *out, int64_t *partials,
+                               int write_total, cudaStream_t st) {
+    const int64_t nb = n > 0 ? (n + kScanTile - 1) / kScanTile : 1;
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, partials);
+    k_scan_partials<<<1, kScanThreads, 0, st>>>(partials, nb);
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, partials, out, write_total);
+    return cudaGetLastError();
+}
+
+// ---- small kernels ----------------------------------------------------------
+
+// dst[i] = src[i] - src[0] for i in [0, n], narrowed to the output pointer type.
+__global__ void k_rebase_colptr_i64(const int64_t *src, int64_t n, int64_t *dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) dst[i] = src[i] - src[0];
+}
+__global__ void k_rebase_colptr_i32(const int64_t *src, int64_t n, int32_t *dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) dst[i] = (int32_t)(src[i] - src[0]);
+}
+
+cudaError_t rebase_colptr(const int64_t *src, int64_t n, void *dst, int dst_is_i64,
+                          cudaStream_t st) {
+    const unsigned nb = (unsigned)((n + 1 + 255) / 256);
+    if (dst_is_i64) k_rebase_colptr_i64<<<nb, 256, 0, st>>>(src, n, (int64_t *)dst);
+    else k_rebase_colptr_i32<<<nb, 256, 0, st>>>(src, n, (int32_t *)dst);
+    return cudaGetLastError();
+}
+
+// Validation of a CSC: colptr monotone from 0 to nnz, rows in [0, nrows).
+template <class I>
+__global__ void k_validate(const I *colptr, const I *rowidx, int64_t ncols, int64_t nrows,
+                           int64_t nnz, int *bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= ncols; i += stride) {
+        const int64_t c = (int64_t)colptr[i];
+        if (i == 0 && c != 0) atomicOr(bad, 1);
+        if (i == ncols && c != nnz) atomicOr(bad, 1);
+        if (i < ncols && (int64_t)colptr[i + 1] < c) atomicOr(bad, 1);
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride) {
+        const int64_t r = (int64_t)rowidx[i];
+        if (r < 0 || r >= nrows) atomicOr(bad, 2);
+    }
+}
+
+cudaError_t validate_csc(const void *colptr, const void *rowidx, int idx64, int64_t ncols,
+                         int64_t nrows, int64_t nnz, int *d_bad, cudaStream_t st) {
+    const unsigned nb = 1024;
+    if (idx64)
+        k_validate<int64_t><<<nb, 256, 0, st>>>((const int64_t *)colptr, (const int64_t *)rowidx,
+                                                ncols, nrows, nnz, d_bad);
+    else
+        k_validate<int32_t><<<nb, 256, 0, st>>>((const int32_t *)colptr, (const int32_t *)rowidx,
+                                                ncols, nrows, nnz, d_bad);
+    return cudaGetLastError();
+}
+
+// w[g] = bytes_per_nnz * (cnt[g] + extra[g]) + ptr_bytes, for g in [0, n).
+__global__ void k_column_bytes(const int64_t *cnt, const int64_t *extra, int64_t n, int64_t r,
+                               int64_t ptr_bytes, int64_t *w) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) w[g] = r * (cnt[g] + (extra ? extra[g] : 0)) + ptr_bytes;
+}
+
+cudaError_t column_bytes(const int64_t *cnt, const int64_t *extra, int64_t n, int64_t r,
+                         int64_t ptr_bytes, int64_t *w, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_column_bytes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cnt, extra, n, r, ptr_bytes, w);
+    return cudaGetLastError();
+}
+
+__global__ void k_add_i64(int64_t *dst, const int64_t *src, int64_t n) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) dst[g] += src[g];
+}
+
+cudaError_t add_i64(int64_t *dst, const int64_t *src, int64_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_add_i64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dst, src, n);
+    return cudaGetLastError();
+}
+
+}  // namespace spg

@@ -1,0 +1,401 @@
+"""Parity of the CUDA path with the CPU oracle, element by element.
+
+Every test here calls the sm_103a library through its C ABI (via the thin
+Python binding) and compares with the oracle on the same seeded inputs:
+structure and per-column nnz bit-exact after the canonical per-column sort,
+integers bit-exact, floats within the stated tolerance (tests/helpers.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from workloads.csc import CSC, from_coo, shuffle_within_columns, column_slice
+
+from helpers import assert_matches, host_csc, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2010_08526_gb300 as spg  # noqa: E402
+
+
+def run(A: CSC, B: CSC, **kw):
+    Ad, Bd = to_dev(A), to_dev(B)
+    C = spg.spgemm(Ad, Bd, validate=True, **kw)
+    torch.cuda.synchronize()
+    return host_csc(C), C.plan_info
+
+
+def check_product(A, B, label, **kw):
+    got, info = run(A, B, **kw)
+    ref, ab = oracle.spgemm(A, B, with_absterm=True)
+    f = oracle.flops_per_column(A, B)
+    assert info["flops"] == int(f.sum()), f"{label}: flops"
+    assert info["nnz_c"] == ref.nnz, f"{label}: nnz"
+    assert_matches(got, ref, ab, f_col=f, label=label)
+    return info
+
+
+def rand_csc(m, n, density, seed, vals="normal", index_dtype=np.int32, value_dtype=np.float64):
+    rng = np.random.default_rng(seed)
+    nnz = int(m * n * density)
+    r = rng.integers(0, m, nnz)
+    c = rng.integers(0, n, nnz)
+    if vals == "normal":
+        v = rng.standard_normal(nnz)
+    elif vals == "ones":
+        v = np.ones(nnz, dtype=np.int64)
+    else:
+        v = rng.integers(-4, 5, nnz).astype(np.int64)
+    a = from_coo(m, n, r, c, v, dup="sum", index_dtype=index_dtype,
+                 value_dtype=value_dtype if vals == "normal" else np.int64)
+    return shuffle_within_columns(a, seed + 3)
+
+
+def skewed(m, n, seed, hubs=3, hub_deg=None, base=4, index_dtype=np.int32, value_dtype=np.float64,
+           dist="normal"):
+    """Random columns plus a few hub rows/columns, so that every tier appears."""
+    rng = np.random.default_rng(seed)
+    hub_deg = hub_deg or max(1, m // 3)
+    rows, cols = [], []
+    counts = rng.integers(0, base * 2 + 1, n)
+    for j in range(n):
+        rows.append(rng.choice(m, size=min(m, int(counts[j])), replace=False))
+        cols.append(np.full(rows[-1].size, j))
+    for h in range(hubs):
+        j = int(rng.integers(0, n))
+        r = rng.choice(m, size=min(m, hub_deg), replace=False)
+        rows.append(r); cols.append(np.full(r.size, j))
+        i = int(rng.integers(0, m))
+        c = rng.choice(n, size=min(n, hub_deg), replace=False)
+        rows.append(np.full(c.size, i)); cols.append(c)
+    r = np.concatenate(rows); c = np.concatenate(cols)
+    if dist == "normal":
+        v = rng.standard_normal(r.size)
+    else:
+        v = np.ones(r.size, dtype=np.int64)
+    a = from_coo(m, n, r, c, v, dup="max", index_dtype=index_dtype,
+                 value_dtype=value_dtype if dist == "normal" else np.int64)
+    return shuffle_within_columns(a, seed + 1)
+
+
+# ------------------------------------------------------------------ plain path
+
+def test_config1_full_size_fp64():
+    A = W.config1()
+    info = check_product(A, A, "config1")
+    assert info["nbatches"] == 1
+
+
+@pytest.mark.parametrize("vt", [np.float64, np.float32, np.int64])
+@pytest.mark.parametrize("it", [np.int32, np.int64])
+def test_types_small(vt, it):
+    dist = "normal" if vt != np.int64 else "int"
+    A = rand_csc(300, 257, 0.03, 5, vals=dist, index_dtype=it, value_dtype=vt)
+    B = rand_csc(257, 301, 0.03, 6, vals=dist, index_dtype=it, value_dtype=vt)
+    check_product(A, B, f"types {vt.__name__} {it.__name__}")
+
+
+@pytest.mark.parametrize("cap", [256, 1024, 8192])
+def test_all_tiers_and_heavy_path(cap):
+    """Skewed matrix: warp, block and heavy tiers in one product; a small
+    hash cap and small panels push many columns through the dense path."""
+    A = skewed(6000, 6000, 11, hubs=4, hub_deg=2500, base=6)
+    tun = spg.Tuning(hash_max_cap=cap, panel_rows=1024)
+    info = check_product(A, A, f"tiers cap={cap}", tuning=tun)
+    if cap == 256:
+        assert info["heavy_columns"] > 0
+
+
+def test_heavy_path_symbolic_panels():
+    """More rows than one symbolic bitmap panel with tiny numeric panels."""
+    A = skewed(3000, 2000, 12, hubs=3, hub_deg=1500, base=3)
+    B = skewed(2000, 500, 13, hubs=2, hub_deg=1000, base=8)
+    tun = spg.Tuning(hash_max_cap=256, panel_rows=1024)
+    check_product(A, B, "rect heavy", tuning=tun)
+
+
+@pytest.mark.parametrize("vt", [np.float32, np.int64])
+def test_heavy_types(vt):
+    dist = "normal" if vt != np.int64 else "ones"
+    A = skewed(5000, 5000, 21, hubs=3, hub_deg=2000, base=5, value_dtype=vt, dist=dist,
+               index_dtype=np.int64)
+    tun = spg.Tuning(hash_max_cap=512, panel_rows=2048)
+    check_product(A, A, f"heavy {vt.__name__}", tuning=tun)
+
+
+def test_tuning_variants():
+    A = skewed(4000, 3000, 31, hubs=2, hub_deg=1500)
+    B = skewed(3000, 3500, 32, hubs=2, hub_deg=1200)
+    for tun in [spg.Tuning(short_seg=1), spg.Tuning(short_seg=64, huge_seg=64),
+                spg.Tuning(block_tier_threads=128), spg.Tuning(block_tier_threads=1024)]:
+        check_product(A, B, f"tuning {tun}", tuning=tun)
+
+
+def test_edge_cases():
+    # empty product
+    Z = CSC(5, 4, np.zeros(5, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    B = CSC(4, 3, np.zeros(4, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    got, info = run(Z, B)
+    assert info["nnz_c"] == 0 and got.nnz == 0 and got.ncols == 3
+    # 1x1
+    A1 = from_coo(1, 1, [0], [0], [3.0])
+    check_product(A1, A1, "1x1")
+    # identity and empty columns
+    A = rand_csc(200, 200, 0.02, 41)
+    I = from_coo(200, 200, np.arange(200), np.arange(200), np.ones(200))
+    check_product(A, I, "A*I")
+    check_product(I, A, "I*A")
+    # zero-sum cancellation stays structural
+    Ac = from_coo(2, 2, [0, 1, 0, 1], [0, 0, 1, 1], [1.0, 1.0, 1.0, -1.0])
+    Bc = from_coo(2, 1, [0, 1], [0, 0], [1.0, 1.0])
+    got, _ = run(Ac, Bc)
+    assert got.nnz == 2
+    # large row indices (sparse rows near the top of the 32-bit key range)
+    rng = np.random.default_rng(7)
+    m = 1 << 26
+    r = rng.integers(m - 5000, m, 3000)
+    c = rng.integers(0, 300, 3000)
+    Ab = from_coo(m, 300, r, c, rng.standard_normal(3000), dup="sum")
+    Bb = rand_csc(300, 50, 0.05, 8)
+    check_product(Ab, Bb, "large rows")
+
+
+def test_row_order_invariance_on_gpu():
+    A = W.config1(n=1024)
+    A2 = shuffle_within_columns(A, 99)
+    g1, _ = run(A, A)
+    g2, _ = run(A2, A2)
+    c1, c2 = oracle.canonical(g1), oracle.canonical(g2)
+    assert np.array_equal(c1.rowidx, c2.rowidx)
+    np.testing.assert_allclose(c1.vals, c2.vals, rtol=1e-12)
+
+
+def test_symbolic_counts_and_invalid_inputs():
+    A = rand_csc(500, 400, 0.01, 51)
+    B = rand_csc(400, 450, 0.01, 52)
+    plan = spg.Plan(to_dev(A), to_dev(B))
+    info = plan.symbolic()
+    cnt = plan.column_counts().cpu().numpy()
+    assert np.array_equal(cnt, oracle.symbolic(A, B))
+    assert info["flops"] == int(oracle.flops_per_column(A, B).sum())
+    plan.check_errors()
+    plan.close()
+    # corrupt column pointers are rejected by validation
+    bad = CSC(A.nrows, A.ncols, A.colptr.copy(), A.rowidx.copy(), A.vals.copy())
+    bad.colptr[5] = bad.colptr[6] + 1
+    with pytest.raises(spg.SpgemmError):
+        spg.Plan(to_dev(bad), to_dev(B), validate=True)
+    badr = CSC(A.nrows, A.ncols, A.colptr.copy(), A.rowidx.copy(), A.vals.copy())
+    badr.rowidx[3] = A.nrows + 5
+    with pytest.raises(spg.SpgemmError):
+        spg.Plan(to_dev(badr), to_dev(B), validate=True)
+    # shape mismatch
+    with pytest.raises(spg.SpgemmError):
+        spg.Plan(to_dev(A), to_dev(A))
+
+
+# --------------------------------------------------------------- k-split + merge
+
+@pytest.mark.parametrize("s", [2, 3, 4, 7])
+def test_ksplit_merge_equals_unsplit(s):
+    A = skewed(3000, 3000, 61, hubs=3, hub_deg=1200)
+    info = check_product(A, A, f"ksplit s={s}", kstages=s)
+    parts = [oracle.spgemm(A, A, krange=kr) for kr in oracle.stage_ranges(3000, s)]
+    assert info["unmerged_nnz"] == sum(p.nnz for p in parts)
+    assert info["flops"] >= info["unmerged_nnz"] >= info["nnz_c"]   # Eq. (1)
+
+
+@pytest.mark.parametrize("vt", [np.float32, np.int64])
+def test_ksplit_heavy_dense_merge(vt):
+    dist = "normal" if vt != np.int64 else "ones"
+    A = skewed(5000, 5000, 71, hubs=4, hub_deg=2500, base=6, value_dtype=vt, dist=dist)
+    tun = spg.Tuning(hash_max_cap=256, panel_rows=1024)
+    check_product(A, A, f"ksplit heavy {vt.__name__}", kstages=4, tuning=tun)
+
+
+def test_merge_api():
+    parts = [rand_csc(700, 300, 0.02, 80 + t) for t in range(4)]
+    M = spg.merge([to_dev(p) for p in parts])
+    torch.cuda.synchronize()
+    ref = oracle.merge(parts)
+    assert_matches(host_csc(M), ref, np.abs(ref.vals) + 1e-300, label="merge")
+    # heavy merge columns
+    big = [skewed(20000, 40, 90 + t, hubs=0, base=1) for t in range(3)]
+    for i, b in enumerate(big):
+        rng = np.random.default_rng(i)
+        r = rng.choice(20000, 12000, replace=False)
+        extra = from_coo(20000, 40, r, np.zeros(r.size, np.int64), rng.standard_normal(r.size))
+        big[i] = oracle.merge([b, extra])
+        big[i] = CSC(20000, 40, big[i].colptr.astype(np.int32), big[i].rowidx.astype(np.int32),
+                     big[i].vals)
+    M = spg.merge([to_dev(p) for p in big])
+    torch.cuda.synchronize()
+    ref = oracle.merge(big)
+    ab = oracle.merge([CSC(p.nrows, p.ncols, p.colptr, p.rowidx, np.abs(p.vals)) for p in big]).vals
+    assert_matches(host_csc(M), ref, ab, label="heavy merge")
+
+
+# ---------------------------------------------------------------- batching
+
+def test_batches_concatenate_to_unbatched():
+    A = W.config1(n=2048)
+    r = 12
+    nnz = int(oracle.symbolic(A, A).sum())
+    inputs = (A.nnz * 2) * r + 2 * (A.ncols + 1) * 4
+    budget = inputs + (1 << 20) + (nnz * r) // 2
+    got, info = run(A, A, budget=budget)
+    assert info["nbatches"] >= 2, info
+    ref, ab = oracle.spgemm(A, A, with_absterm=True)
+    assert_matches(got, ref, ab, label="batched")
+
+
+def test_budget_too_small():
+    A = W.config1(n=1024)
+    with pytest.raises(spg.SpgemmError):
+        run(A, A, budget=1 << 10)
+
+
+def test_run_batched_streams_to_host():
+    A = skewed(3000, 3000, 101, hubs=2, hub_deg=1000)
+    Ad = to_dev(A)
+    ref, ab = oracle.spgemm(A, A, with_absterm=True)
+    budget = A.bytes() * 2 + (1 << 20) + ref.nnz * 12
+    for kst in (1, 3):
+        plan = spg.Plan(Ad, Ad, budget=budget, kstages=kst, host_slot_bytes=1 << 16, host_slots=2)
+        info = plan.symbolic()
+        pieces = []
+
+        def sink(batch, c0, c1, arrs):
+            cp, ri, va = arrs
+            pieces.append((batch, c0, c1, cp.copy(), ri.copy(), va.copy()))
+            return 0
+
+        spg.run_batched(plan, sink)
+        assert pieces[0][1] == 0 and pieces[-1][2] == A.ncols
+        for a, b in zip(pieces, pieces[1:]):
+            assert a[2] == b[1] and b[0] >= a[0]
+        colptr = [0]
+        for _, c0, c1, cp, ri, va in pieces:
+            colptr.extend((cp[1:] + colptr[-1]).tolist())
+        got = CSC(A.nrows, A.ncols, np.array(colptr, np.int64),
+                  np.concatenate([p[4] for p in pieces]).astype(np.int64),
+                  np.concatenate([p[5] for p in pieces]))
+        assert_matches(got, ref, ab, label=f"run_batched s={kst}")
+        assert len({p[0] for p in pieces}) == info["nbatches"]
+        plan.close()
+
+
+def test_sink_error_stops_cleanly():
+    A = skewed(2000, 2000, 111, hubs=2, hub_deg=800)
+    Ad = to_dev(A)
+    plan = spg.Plan(Ad, Ad, host_slot_bytes=1 << 14, host_slots=2)
+    plan.symbolic()
+    calls = []
+
+    def sink(batch, c0, c1, arrs):
+        calls.append(c0)
+        return 1 if len(calls) == 2 else 0
+
+    with pytest.raises(spg.SpgemmError):
+        spg.run_batched(plan, sink)
+    assert len(calls) == 2
+    # the plan stays usable
+    C = plan.numeric(0)
+    torch.cuda.synchronize()
+    assert C.nnz == plan.batch(0)[2]
+    plan.close()
+
+
+# ---------------------------------------------------------------- backward
+
+def test_backward_matches_oracle():
+    A, B = W.config5(m=3000, k=3000, n=1500, value_dtype=np.float64)
+    C = oracle.spgemm(A, B)
+    G = shuffle_within_columns(W.values_on_pattern(C, 17, dist="normal", value_dtype=np.float64), 5)
+    dA, dB = spg.backward(to_dev(A), to_dev(B), to_dev(G))
+    torch.cuda.synchronize()
+    rA, rB = oracle.backward(A, B, G)
+    np.testing.assert_allclose(dA.cpu().numpy(), rA, rtol=1e-11, atol=1e-11)
+    np.testing.assert_allclose(dB.cpu().numpy(), rB, rtol=1e-11, atol=1e-11)
+
+
+def test_backward_heavy_columns():
+    A = skewed(4000, 3000, 121, hubs=2, hub_deg=2000)
+    B = skewed(3000, 200, 122, hubs=1, hub_deg=2500)
+    C = oracle.spgemm(A, B)
+    G = W.values_on_pattern(C, 18, dist="normal", value_dtype=np.float64)
+    Ad, Bd = to_dev(A), to_dev(B)
+    plan = spg.Plan(Ad, Bd, tuning=spg.Tuning(hash_max_cap=256, panel_rows=1024))
+    dA, dB = plan.backward(to_dev(G))
+    torch.cuda.synchronize()
+    rA, rB = oracle.backward(A, B, G)
+    np.testing.assert_allclose(dA.cpu().numpy(), rA, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(dB.cpu().numpy(), rB, rtol=1e-10, atol=1e-10)
+    plan.close()
+
+
+def test_autograd_function_fp64_finite_differences():
+    A, B = W.config5(m=64, k=64, n=64, value_dtype=np.float64)
+    Ad, Bd = to_dev(A), to_dev(B)
+    a = Ad.vals.clone().requires_grad_(True)
+    b = Bd.vals.clone().requires_grad_(True)
+    c = spg.SpGEMMFn.apply(a, b, Ad, Bd)
+    torch.manual_seed(0)
+    gvals = torch.randn(c.shape, dtype=torch.float64, device="cuda")
+    (c * gvals).sum().backward()
+    for recompute in (False, True):
+        a2 = Ad.vals.clone().requires_grad_(True)
+        b2 = Bd.vals.clone().requires_grad_(True)
+        c2 = spg.SpGEMMFn.apply(a2, b2, Ad, Bd, recompute)
+        (c2 * gvals).sum().backward()
+        torch.testing.assert_close(a2.grad, a.grad, rtol=1e-12, atol=1e-12)
+    # central differences of the bilinear loss are exact up to rounding
+    h = 1e-3
+    with torch.no_grad():
+        for q in range(0, A.nnz, 97):
+            ap = Ad.vals.clone(); ap[q] += h
+            am = Ad.vals.clone(); am[q] -= h
+            lp = (spg.SpGEMMFn.apply(ap, Bd.vals, Ad, Bd) * gvals).sum()
+            lm = (spg.SpGEMMFn.apply(am, Bd.vals, Ad, Bd) * gvals).sum()
+            fd = float((lp - lm) / (2 * h))
+            assert abs(fd - float(a.grad[q])) <= 1e-9 * max(1.0, abs(fd))
+    # and the gradient equals the oracle's masked products, with G in the
+    # library's (unsorted) layout of C, which is the layout of SpGEMMFn's output
+    plan = spg.Plan(Ad, Bd)
+    plan.symbolic()
+    Cl = plan.numeric(0)
+    Gl = CSC(Cl.nrows, Cl.ncols, Cl.colptr.cpu().numpy().astype(np.int64),
+             Cl.rowidx.cpu().numpy().astype(np.int64), gvals.cpu().numpy())
+    rA, rB = oracle.backward(A, B, Gl)
+    np.testing.assert_allclose(a.grad.cpu().numpy(), rA, rtol=1e-11, atol=1e-11)
+    np.testing.assert_allclose(b.grad.cpu().numpy(), rB, rtol=1e-11, atol=1e-11)
+    plan.close()
+
+
+# ---------------------------------------------------------------- batched problems
+
+def test_multi_path_counting_exact():
+    probs = W.config4(count=24, nmax=5000)
+    dev = [to_dev(p) for p in probs]
+    for use_graph in (False, True):
+        M = spg.Multi(dev, dev)
+        M.run(use_graph=use_graph)
+        M.run(use_graph=use_graph)   # replay
+        torch.cuda.synchronize()
+        cp, ri, va = M.output()
+        cp = cp.cpu().numpy(); ri = ri.cpu().numpy(); va = va.cpu().numpy()
+        col = 0
+        for p in probs:
+            ref = oracle.spgemm(p, p)
+            a, b = cp[col], cp[col + p.ncols]
+            got = CSC(p.nrows, p.ncols, cp[col:col + p.ncols + 1] - a, ri[a:b].astype(np.int64), va[a:b])
+            assert_matches(got, ref, exact=True, label="multi")
+            col += p.ncols
+        M.close()
