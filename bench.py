@@ -1,0 +1,472 @@
+"""Benchmark of the memory-constrained SpGEMM hot path on one GB300.
+
+Workload (one step): C = A*A for A = R-MAT scale 20 (1,048,576 x 1,048,576,
+edge factor 16, a=0.57 b=c=0.19 d=0.05, symmetrised, duplicates summed),
+float32 values accumulated in float32, int32 CSC. A step runs the whole
+path: flop count and tier binning, symbolic count per column, batch plan for
+the HBM budget, row-panel copy of A, and the numeric hash / dense kernels for
+every batch. Inputs (250 MB) and outputs (~190 GB) are far larger than L2, so
+no flush is needed between steps.
+
+value : SpGEMM GFLOP/s (2 x multiplications / step time), inputs resident.
+e2e   : the same metric through the C ABI with host buffers: every step copies
+        A from pinned host memory, runs symbolic + the batch loop that streams
+        every column batch of C to pinned host slots (spgemm_run_batched), and
+        reads the result back on the host.
+
+Extra keys: the k-split path (4 stages + sort-free hash merge) on the same
+workload, the batched persistent launch (512 uneven products in one CUDA
+graph) vs 512 plain per-matrix launches, and forward + masked backward vs
+gradients formed by plain SpGEMMs.
+
+--impl reference times the CPU oracle (the plain Gustavson definition) on the
+host cores on a bounded column sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "SpGEMM GFLOP/s (2 x multiplies / s)"
+UNIT = "GFLOP/s"
+WORKLOAD = ("C = A*A, A R-MAT scale 20 (1,048,576^2, edge factor 16, a=.57 b=c=.19 d=.05), "
+            "symmetrised, duplicates summed, fp32 U(0,1) accumulated in fp32, int32 CSC")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", os.environ.get("BENCH_GPU_INDEX", "0")],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- helpers
+def algorithmic_bytes_dense(A, f, cnt, cap, si=4, sv=4):
+    """Column-Gustavson bytes of the dense (heavy) numeric kernel: per dense
+    column j, its B entries (index + value) and two colptr reads of A per B
+    entry, every gathered A entry (index + value), and every written C entry
+    (index + value)."""
+    dense = cnt > cap
+    nnzb = np.diff(A.colptr.astype(np.int64))
+    b_bytes = int(nnzb[dense].sum()) * (si + sv + 2 * si)
+    a_bytes = int(f[dense].sum()) * (si + sv)
+    c_bytes = int(cnt[dense].sum()) * (si + sv)
+    return b_bytes + a_bytes + c_bytes, int(dense.sum())
+
+
+def flops_host(A):
+    deg = np.diff(A.colptr.astype(np.int64))
+    cols = np.repeat(np.arange(A.ncols), deg)
+    return np.bincount(cols, weights=deg[A.rowidx.astype(np.int64)].astype(np.float64),
+                       minlength=A.ncols).astype(np.int64)
+
+
+def dist_init(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- reference arm
+def cpu_oracle_sample(A, f, target_flops):
+    """Time the oracle (as it stands) on a contiguous column range of about
+    target_flops multiplications; returns (GFLOP/s, sample description, cores)."""
+    import oracle
+    from workloads.csc import column_slice
+    rng = np.random.default_rng(0)
+    c0 = int(rng.integers(0, A.ncols // 2))
+    cs = np.cumsum(f[c0:])
+    c1 = c0 + int(np.searchsorted(cs, target_flops)) + 1
+    c1 = min(c1, A.ncols)
+    Bs = column_slice(A, c0, c1)
+    fl = int(f[c0:c1].sum())
+    cores = oracle.num_threads()
+    t0 = time.perf_counter()
+    C = oracle.spgemm(A, Bs)
+    dt = time.perf_counter() - t0
+    desc = (f"columns [{c0}, {c1}) of the workload ({c1 - c0} columns, {fl:.3e} multiplies, "
+            f"nnz(C) {C.nnz}), oracle symbolic + numeric, float64 accumulation")
+    return 2 * fl / dt / 1e9, desc, cores, dt
+
+
+def run_reference(args):
+    rank, world = dist_init(args.gpus)
+    if rank != 0:
+        return
+    A = W.config2()
+    f = flops_host(A)
+    vals = []
+    desc = cores = None
+    for i in range(args.warmup + args.steps):
+        v, desc, cores, _ = cpu_oracle_sample(A, f, args.ref_flops)
+        if i >= args.warmup:
+            vals.append(v)
+    v = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "scaling": "weak", "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "oracle": "plain CPU Gustavson with a dense accumulator"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "vs_baseline": None,
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import paper_2010_08526_gb300 as spg
+
+    rank, world = dist_init(args.gpus)
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    os.environ["BENCH_GPU_INDEX"] = str(dev)
+    A = W.config2()
+    f = flops_host(A)
+    F = int(f.sum())
+    st = torch.cuda.current_stream()
+
+    Ad = spg.Csc.from_host(A, device=f"cuda:{dev}")
+    plan = spg.Plan(Ad, Ad)
+    plan.set_timing(True)
+    info = plan.symbolic()
+    assert info["flops"] == F
+    outs = [plan.alloc_batch(t) for t in range(plan.nbatches)]
+
+    def step():
+        plan.symbolic()
+        for t in range(plan.nbatches):
+            plan.numeric(t, out=outs[t])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.stats(reset=True)
+    plan.check_errors()
+    clk = ClockSampler()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world)
+    stats = plan.stats(reset=True)
+    plan.check_errors()
+    value = world * 2 * F / (ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel (dense row-panel numeric)
+    cnt = plan.column_counts().cpu().numpy()
+    hbm, peak_kind = peaks()
+    dense_ms = stats["ms"]["num_dense"] / max(1, stats["count"]["num_dense"])
+    bytes_dense, ndense = algorithmic_bytes_dense(A, f, cnt, 8192)
+    launches_dense = max(1, stats["count"]["num_dense"] // args.steps)
+    bytes_per_launch = bytes_dense / launches_dense
+    achieved = bytes_per_launch / (dense_ms / 1e3) / 1e9 if dense_ms > 0 else 0.0
+    phase_ms = {k: round(v / args.steps, 3) for k, v in stats["ms"].items() if v}
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic_num_dense.txt")
+    if os.path.exists(tf):
+        for line in open(tf):
+            if line.startswith("bytes_per_full_launch"):
+                traffic = float(line.split()[1])
+
+    # ---- k-split (4 stages + hash merge) on the same workload
+    ks = None
+    if not args.quick:
+        del outs
+        torch.cuda.empty_cache()
+        kplan = spg.Plan(Ad, Ad, kstages=4)
+        kinfo = kplan.symbolic()
+        kouts = [kplan.alloc_batch(t) for t in range(kplan.nbatches)]
+
+        def kstep():
+            kplan.symbolic()
+            for t in range(kplan.nbatches):
+                kplan.numeric(t, out=kouts[t])
+        kstep()
+        torch.cuda.synchronize()
+        ks_steps = max(1, args.steps // 2)
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(st)
+        for _ in range(ks_steps):
+            kstep()
+        k1.record(st)
+        torch.cuda.synchronize()
+        kms = k0.elapsed_time(k1) / ks_steps
+        kplan.check_errors()
+        ks = {"value": 2 * F / (kms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": kms,
+              "stages": 4, "nbatches": kinfo["nbatches"], "unmerged_nnz": kinfo["unmerged_nnz"]}
+        del kouts
+        kplan.close()
+        torch.cuda.empty_cache()
+        outs = None
+
+    # ---- e2e through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        if outs is not None:
+            del outs
+            torch.cuda.empty_cache()
+        hostA = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+                 for x in (A.colptr, A.rowidx, A.vals)]
+        dA = spg.Csc(A.nrows, A.ncols, *[torch.empty_like(h, device=f"cuda:{dev}") for h in hostA])
+        eplan = spg.Plan(dA, dA, host_slot_bytes=256 << 20, host_slots=4)
+        copy_stream = torch.cuda.Stream()
+        got = {"bytes": 0, "check": 0.0}
+
+        def sink(batch, c0, c1, arrs):
+            cp, ri, va = arrs
+            got["bytes"] += cp.nbytes + ri.nbytes + va.nbytes
+            if va.size:
+                got["check"] += float(va[0])
+            return 0
+
+        def estep():
+            for h, d in zip(hostA, (dA.colptr, dA.rowidx, dA.vals)):
+                d.copy_(h, non_blocking=True)
+            eplan.symbolic()
+            got["bytes"] = 0
+            spg.run_batched(eplan, sink, copy=copy_stream)
+            return got["bytes"]
+
+        estep()
+        torch.cuda.synchronize()
+        e_steps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        bo = 0
+        for _ in range(e_steps):
+            bo = estep()
+        torch.cuda.synchronize()
+        edt = (time.perf_counter() - t0) / e_steps
+        bi = sum(h.numel() * h.element_size() for h in hostA)
+        e2e = {"value": world * 2 * F / edt / 1e9, "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "ms_per_step": edt * 1e3,
+               "d2h_gbs": bo / edt / 1e9}
+        eplan.close()
+
+    # ---- batched persistent launch vs plain per-matrix path; fwd+bwd vs plain
+    extras = {}
+    if not args.quick:
+        extras["batched_vs_plain"] = bench_multi(spg, torch, args)
+        extras["fwdbwd_vs_plain"] = bench_fwdbwd(spg, torch, args)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, desc, cores, dt = cpu_oracle_sample(A, f, args.ref_flops)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "flops_per_step": F, "nnz_c": info["nnz_c"],
+                       "nbatches": info["nbatches"], "budget": "80% of free HBM",
+                       "l2": "inputs and outputs larger than L2 (no flush needed)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "kernel": "k_num_dense (dense row-panel numeric)",
+                         "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "launch_ms": dense_ms, "dense_columns": ndense},
+            "phase_ms_per_step": phase_ms,
+            "gpu_launches": stats["launches"],
+            "clocks": clocks,
+            "e2e": e2e,
+            "ksplit4": ks,
+            "cpu_baseline": cpu,
+        }
+        line.update(extras)
+        print(json.dumps(line))
+
+
+def bench_multi(spg, torch, args):
+    """512 uneven G(n,p) products (int64 ones semiring): one CUDA-graph
+    launch of the device-driven multi-problem pass vs 512 plain plans."""
+    n = 512 if not args.small_extras else 64
+    probs = W.config4(count=n, nmax=200000 if not args.small_extras else 20000)
+    dev = [spg.Csc.from_host(p) for p in probs]
+    flops = sum(int(flops_host(p).sum()) for p in probs)
+    M = spg.Multi(dev, dev)
+    M.run(use_graph=True)
+    torch.cuda.synchronize()
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        M.run(use_graph=True)
+    torch.cuda.synchronize()
+    t_multi = (time.perf_counter() - t0) / reps
+    M.close()
+    torch.cuda.empty_cache()
+
+    def plain():
+        for d in dev:
+            C = spg.spgemm(d, d)
+            del C
+    plain()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain()
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    return {"problems": n, "flops": flops, "multi_ms": t_multi * 1e3, "plain_ms": t_plain * 1e3,
+            "speedup": t_plain / t_multi, "multi_gflops": 2 * flops / t_multi / 1e9}
+
+
+def bench_fwdbwd(spg, torch, args):
+    """Forward + masked backward (SpGEMMFn) vs gradients formed by plain
+    SpGEMMs G*B^T and A^T*G on explicit transposes, masked afterwards."""
+    import oracle  # noqa: F401  (not used: inputs only)
+    from workloads.csc import transpose
+    A, B = W.config5()
+    Ad, Bd = spg.Csc.from_host(A), spg.Csc.from_host(B)
+    At, Bt = spg.Csc.from_host(transpose(A)), spg.Csc.from_host(transpose(B))
+    torch.manual_seed(0)
+
+    def fused():
+        a = Ad.vals.detach().clone().requires_grad_(True)
+        b = Bd.vals.detach().clone().requires_grad_(True)
+        c = spg.SpGEMMFn.apply(a, b, Ad, Bd)
+        c.backward(torch.ones_like(c))
+        return a.grad, b.grad
+
+    def plain():
+        C = spg.spgemm(Ad, Bd)
+        G = spg.Csc(C.nrows, C.ncols, C.colptr, C.rowidx, torch.ones_like(C.vals))
+        gb = spg.spgemm(G, Bt)          # G * B^T  (m x k), masked to pattern(A) by the caller
+        ag = spg.spgemm(At, G)          # A^T * G  (k x n), masked to pattern(B)
+        return gb, ag
+
+    for fn in (fused, plain):
+        fn()
+    torch.cuda.synchronize()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fused()
+    torch.cuda.synchronize()
+    tf = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        plain()
+    torch.cuda.synchronize()
+    tp = (time.perf_counter() - t0) / reps
+    return {"fused_ms": tf * 1e3, "plain_ms": tp * 1e3, "speedup": tp / tf,
+            "note": "plain path = forward SpGEMM + two full SpGEMMs on transposes (mask not applied)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the k-split and extra sections")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--small-extras", action="store_true")
+    ap.add_argument("--ref-flops", type=float, default=1.2e10,
+                    help="multiplications in the CPU oracle sample")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -132,6 +132,21 @@ typedef struct {
     int64_t heavy_columns;    /* columns handled by the dense row-panel accumulator */
 } spgemm_plan_info;
 
+/*
+ * Per-phase statistics of a plan (kernel launches always; device time only
+ * while timing is enabled). Phases: 0 flop count + binning, 1 symbolic hash
+ * tiers, 2 symbolic bitmap (heavy columns), 3 scans, 4 row-panel copy of A,
+ * 5 numeric hash tiers, 6 numeric dense row panels, 7 stage merge,
+ * 8 backward. Times come from CUDA events recorded on the stream each phase
+ * was launched on.
+ */
+#define SPGEMM_NUM_PHASES 9
+typedef struct {
+    int64_t launches;                  /* kernel launches since the last reset */
+    double ms[SPGEMM_NUM_PHASES];      /* summed device time per phase */
+    int64_t count[SPGEMM_NUM_PHASES];  /* timed instances per phase */
+} spgemm_stats;
+
 /* Thread-local message of the last failing call (never NULL). */
 const char *spgemm_last_error(void);
 
@@ -194,6 +209,18 @@ spgemm_status spgemm_plan_colptr(const spgemm_plan *plan, void *colptr_out,
  * (internal consistency guards; neither happens on valid input).
  */
 spgemm_status spgemm_plan_check(const spgemm_plan *plan, cudaStream_t stream);
+
+/*
+ * Enable (1) or disable (0) per-phase event timing on the plan. Timing adds
+ * two event records per phase; results are read with spgemm_plan_stats.
+ */
+spgemm_status spgemm_plan_set_timing(spgemm_plan *plan, int enable);
+
+/*
+ * Read the plan's statistics (waits for the timed events to complete), then
+ * clear them when reset != 0.
+ */
+spgemm_status spgemm_plan_stats(spgemm_plan *plan, int reset, spgemm_stats *out);
 
 /*
  * spgemm_numeric -- compute batch t of C (columns [col_begin, col_end) of the

@@ -50,6 +50,18 @@ class SpgemmPlanInfo(ctypes.Structure):
     ]
 
 
+NUM_PHASES = 9
+PHASES = ["flops_bin", "sym_hash", "sym_heavy", "scan", "panels", "num_hash", "num_dense",
+          "merge", "backward"]
+
+
+class SpgemmStats(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_int64), ("ms", ctypes.c_double * NUM_PHASES),
+        ("count", ctypes.c_int64 * NUM_PHASES),
+    ]
+
+
 SINK_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                            ctypes.c_int64, ctypes.POINTER(SpgemmCsc))
 
@@ -69,6 +81,8 @@ SIGNATURES = {
     "spgemm_plan_column_counts": (ctypes.c_int, [vp, vp, vp]),
     "spgemm_plan_check": (ctypes.c_int, [vp, vp]),
     "spgemm_plan_colptr": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
+    "spgemm_plan_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+    "spgemm_plan_stats": (ctypes.c_int, [vp, ctypes.c_int, P(SpgemmStats)]),
     "spgemm_numeric": (ctypes.c_int, [vp, i64, P(SpgemmCsc), vp]),
     "spgemm_merge": (ctypes.c_int, [P(SpgemmCsc), ctypes.c_int, P(SpgemmCsc), vp]),
     "spgemm_run_batched": (ctypes.c_int, [vp, SINK_FN, vp, vp, vp]),

@@ -176,6 +176,17 @@ class Plan:
                                                   _stream_handle(stream)))
         return out
 
+    def set_timing(self, enable: bool = True):
+        check(self._lib.spgemm_plan_set_timing(self._h, int(enable)))
+
+    def stats(self, reset: bool = False) -> dict:
+        """Kernel launches and per-phase device milliseconds."""
+        s = C.SpgemmStats()
+        check(self._lib.spgemm_plan_stats(self._h, int(reset), ctypes.byref(s)))
+        return {"launches": int(s.launches),
+                "ms": {C.PHASES[i]: float(s.ms[i]) for i in range(C.NUM_PHASES)},
+                "count": {C.PHASES[i]: int(s.count[i]) for i in range(C.NUM_PHASES)}}
+
     def check_errors(self, stream=None):
         """Synchronise and raise if a kernel recorded an error flag."""
         check(self._lib.spgemm_plan_check(self._h, _stream_handle(stream)))

@@ -44,6 +44,7 @@ void PlanState::release_all() {
     for (auto &b : ring_val) b.release();
     for (auto &h : host_slots) h.release();
     ring_col.clear(); ring_row.clear(); ring_val.clear(); host_slots.clear();
+    timer.release();
 }
 
 static int value_bytes(spgemm_value_t v) { return v == SPGEMM_F32 ? 4 : 8; }
@@ -126,7 +127,7 @@ spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B, const
     ps.dev = dev; ps.nsm = prop.multiProcessorCount;
     // tuning
     const spgemm_tuning *tu = opts ? opts->tuning : nullptr;
-    ps.tun.log2R = value_bytes((spgemm_value_t)ps.vtype) == 4 ? 15 : 14;
+    ps.tun.log2R = value_bytes((spgemm_value_t)ps.vtype) == 4 ? 14 : 13;
     if (tu) {
         if (tu->hash_max_cap) ps.tun.hash_cap_max = tu->hash_max_cap;
         if (tu->panel_rows) {
@@ -142,7 +143,7 @@ spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B, const
         bool ok = false;
         for (int c = 256; c <= 8192; c <<= 1) ok |= ps.tun.hash_cap_max == c;
         const int R = 1 << ps.tun.log2R;
-        const int dense_smem = R * value_bytes((spgemm_value_t)ps.vtype) + R / 8;
+        const int dense_smem = R * value_bytes((spgemm_value_t)ps.vtype) + R;
         if (!ok || ps.tun.log2R < 10 || ps.tun.log2R > 16 || dense_smem > 200 * 1024 ||
             ps.tun.short_seg < 1 || ps.tun.short_seg > 64 || ps.tun.huge_seg < 64 ||
             (ps.tun.block_threads && (ps.tun.block_threads % 32 || ps.tun.block_threads < 128 ||
@@ -156,7 +157,7 @@ spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B, const
     const int64_t R = 1LL << ps.tun.log2R;
     ps.P = (int)((ps.m + R - 1) / R);
     if (ps.P < 1) ps.P = 1;
-    const int64_t maxbm = (int64_t)(192 * 1024) * 8;   // bitmap rows per CTA
+    const int64_t maxbm = (int64_t)(160 * 1024) * 8;   // bitmap rows per CTA
     const int64_t mpad = ((ps.m + R - 1) / R) * R;
     ps.Rs = mpad <= maxbm ? (mpad > 0 ? mpad : R) : (maxbm / R) * R;
     ps.Q = (int)((ps.m + ps.Rs - 1) / ps.Rs);
@@ -296,6 +297,15 @@ spgemm_status spgemm_numeric(spgemm_plan *plan, int64_t t, spgemm_csc *C, cudaSt
 spgemm_status spgemm_backward(spgemm_plan *plan, const spgemm_csc *G, void *dA_vals, void *dB_vals,
                               cudaStream_t stream) {
     if (!plan || !G) { set_error("NULL argument"); return SPGEMM_ERR_INVALID; }
+    const PlanState &ps = plan->ps;
+    spgemm_status s = check_csc(G, "G", false);
+    if (s != SPGEMM_OK) return s;
+    if (G->nrows != ps.m || G->ncols != ps.n) { set_error("G must have C's shape"); return SPGEMM_ERR_INVALID; }
+    if (G->idx_type != (ps.idx64 ? SPGEMM_I64 : SPGEMM_I32) || G->val_type != ps.vtype) {
+        set_error("G must share the plan's index and value types"); return SPGEMM_ERR_INVALID;
+    }
+    if ((ps.A.nnz && !dA_vals) || (ps.B.nnz && !dB_vals)) { set_error("NULL gradient buffer"); return SPGEMM_ERR_INVALID; }
+    if (ps.s != 1) { set_error("backward works on plans with one stage"); return SPGEMM_ERR_INVALID; }
     return plan->ps.eng->backward(plan->ps, G, dA_vals, dB_vals, stream);
 }
 
@@ -328,6 +338,22 @@ spgemm_status spgemm_plan_colptr(const spgemm_plan *plan, void *colptr_out, spge
     }
     cudaError_t e = rebase_colptr(ps.colptr.as<int64_t>(), ps.n, colptr_out, ptr_type == SPGEMM_I64, stream);
     return e == cudaSuccess ? SPGEMM_OK : cuda_fail(e, "rebase_colptr");
+}
+
+spgemm_status spgemm_plan_set_timing(spgemm_plan *plan, int enable) {
+    if (!plan) { set_error("plan is NULL"); return SPGEMM_ERR_INVALID; }
+    plan->ps.timer.enabled = enable != 0;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_plan_stats(spgemm_plan *plan, int reset, spgemm_stats *out) {
+    if (!plan || !out) { set_error("NULL argument"); return SPGEMM_ERR_INVALID; }
+    PhaseTimer &tm = plan->ps.timer;
+    tm.collect();
+    out->launches = tm.launches;
+    for (int i = 0; i < SPGEMM_NUM_PHASES; ++i) { out->ms[i] = tm.ms[i]; out->count[i] = tm.count[i]; }
+    if (reset) tm.reset();
+    return SPGEMM_OK;
 }
 
 spgemm_status spgemm_plan_check(const spgemm_plan *plan, cudaStream_t stream) {

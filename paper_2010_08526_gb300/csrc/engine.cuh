@@ -43,10 +43,16 @@ struct Ctx {
     int32_t *h_small;    // pinned host, >= 64 ints
     int P, Q;
     int64_t Rs;
+    PhaseTimer *tm = nullptr;   // optional phase timing and launch counting
+    int ph_hash = kPhNumHash, ph_dense = kPhNumDense;
+    int tbegin(int phase, cudaStream_t st) const { return tm ? tm->begin(phase, st) : -1; }
+    void tend(int idx, cudaStream_t st) const { if (tm) tm->end(idx, st); }
+    void launched(int n = 1) const { if (tm) tm->launches += n; }
 };
 
 inline Ctx make_ctx(PlanState &ps) {
     Ctx c;
+    c.tm = &ps.timer;
     c.nsm = ps.nsm; c.tun = ps.tun; c.err = ps.err.as<int>();
     c.hist = ps.hist.as<int32_t>(); c.cursor = ps.cursor.as<int32_t>();
     c.h_small = ps.h_small.as<int32_t>();
@@ -64,8 +70,17 @@ inline TierCommon common_of(const Ctx &c) {
     return t;
 }
 
-template <class K> static void set_smem(K kern, int bytes) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+// Allow a kernel the largest dynamic shared memory the device permits next to
+// its static shared memory (opt-in maximum minus static size).
+template <class K> static void set_smem(K kern, int) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess && optin > (int)fa.sharedSizeBytes)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+    cudaGetLastError();   // attribute calls must not leave a sticky error behind
 }
 
 // Output of a numeric pass.
@@ -142,7 +157,7 @@ template <class I, class V> struct Engine : EngineBase {
         }
         const int thr = block_tier_threads(T, cx.tun);
         const int smem = T * 4;
-        const int per_sm = std::max(1, std::min(2048 / thr, (200 * 1024) / smem));
+        const int per_sm = std::max(1, std::min(2048 / thr, (228 * 1024) / (smem + 34 * 1024)));
         const int want = count < 0 ? cx.nsm * per_sm : count;
         const int blocks = std::max(1, std::min(want, cx.nsm * per_sm));
         switch (T) {
@@ -169,7 +184,7 @@ template <class I, class V> struct Engine : EngineBase {
         }
         const int thr = block_tier_threads(T, cx.tun);
         const int smem = T * (int)(4 + sizeof(V));
-        const int per_sm = std::max(1, std::min(2048 / thr, (220 * 1024) / smem));
+        const int per_sm = std::max(1, std::min(2048 / thr, (228 * 1024) / (smem + 34 * 1024)));
         const int want = count < 0 ? cx.nsm * per_sm : count;
         const int blocks = std::max(1, std::min(want, cx.nsm * per_sm));
         switch (T) {
@@ -184,7 +199,7 @@ template <class I, class V> struct Engine : EngineBase {
 
     static int dense_smem(const Ctx &cx) {
         const int R = 1 << cx.tun.log2R;
-        return R * (int)sizeof(V) + R / 8;
+        return R * (int)sizeof(V) + R;
     }
 
     // ---- symbolic pass -------------------------------------------------------
@@ -201,11 +216,14 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(cudaMemsetAsync(cx.hist, 0, sizeof(int32_t) * 64, st));
         SPG_CK(cudaMemsetAsync(cx.cursor, 0, sizeof(int32_t) * 64, st));
         if (nc > 0) {
+            const int tb = cx.tbegin(kPhFlopsBin, st);
             k_flops_bin<Src><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
                 sa, c_lo, c_hi, cx.tun.hash_cap_max, bound, f_out, tier, cnt_out, cx.hist);
             k_bin_scatter<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(tier, c_lo, c_hi, cx.hist,
                                                                        cx.cursor, list, off,
                                                                        heavy_ord_w);
+            cx.tend(tb, st);
+            cx.launched(2);
             SPG_CK(cudaGetLastError());
         }
         SPG_CK(cudaMemcpyAsync(cx.h_small, cx.hist, sizeof(int32_t) * 16, cudaMemcpyDeviceToHost, st));
@@ -218,8 +236,10 @@ template <class I, class V> struct Engine : EngineBase {
         for (int t = kHeavyTier0; t < kTiers; ++t) nheavy += hist[t];
         TierCommon c = common_of(cx);
         c.list = list; c.list_off = off; c.cnt = cnt_out;
+        const int th = cx.tbegin(kPhSymHash, st);
         for (int t = 1; t <= 8; ++t)
-            if (hist[t]) launch_sym_tier<Src>(cx, sa, c, t, hist[t], st);
+            if (hist[t]) { launch_sym_tier<Src>(cx, sa, c, t, hist[t], st); cx.launched(); }
+        cx.tend(th, st);
         if (nheavy) {
             if (pcnt_grow) {
                 SPG_CK(pcnt_grow->ensure(sizeof(int32_t) * (size_t)nheavy * cx.P));
@@ -230,7 +250,10 @@ template <class I, class V> struct Engine : EngineBase {
             const int64_t items = (int64_t)nheavy * cx.Q;
             const int smem = (int)(((cx.Rs + 31) / 32) * 4);
             const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(items, cx.nsm));
+            const int tb = cx.tbegin(kPhSymHeavy, st);
             k_sym_bitmap<Src><<<blocks, 1024, smem, st>>>(sa, c);
+            cx.tend(tb, st);
+            cx.launched();
         }
         SPG_CK(cudaGetLastError());
         return SPGEMM_OK;
@@ -254,6 +277,7 @@ template <class I, class V> struct Engine : EngineBase {
         c.colptr = o.colptr;
         c.out_base = o.out_base;
         if (any_hash && nc > 0) {
+            const int th = cx.tbegin(cx.ph_hash, st);
             SPG_CK(cudaMemsetAsync(cx.hist, 0, sizeof(int32_t) * 64, st));
             SPG_CK(cudaMemsetAsync(cx.cursor, 0, sizeof(int32_t) * 64, st));
             k_numeric_tier<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
@@ -265,8 +289,10 @@ template <class I, class V> struct Engine : EngineBase {
             for (int t = 1; t <= 8; ++t) {
                 if (tier_cap(t) > cx.tun.hash_cap_max) break;
                 const int cntt = tc ? tc[t] : -1;
-                if (cntt != 0) launch_num_tier<Src>(cx, sa, c, t, cntt, o.rows, o.vals, st);
+                if (cntt != 0) { launch_num_tier<Src>(cx, sa, c, t, cntt, o.rows, o.vals, st); cx.launched(); }
             }
+            cx.launched(2);
+            cx.tend(th, st);
         }
         if (heavy) {
             c.list = sym_list; c.list_off = sym_off;
@@ -275,8 +301,11 @@ template <class I, class V> struct Engine : EngineBase {
             c.pcnt_in = pcnt_in;
             c.c_lo = c_lo; c.c_hi = c_hi;
             const int smem = dense_smem(cx);
-            const int per_sm = std::max(1, std::min(2, (220 * 1024) / smem));
-            k_num_dense<DSrc><<<cx.nsm * per_sm, 1024, smem, st>>>(da, c, o.rows, o.vals);
+            const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 34 * 1024)));
+            const int td = cx.tbegin(cx.ph_dense, st);
+            k_num_dense<DSrc><<<cx.nsm * per_sm, 512, smem, st>>>(da, c, o.rows, o.vals);
+            cx.tend(td, st);
+            cx.launched();
         }
         SPG_CK(cudaGetLastError());
         return SPGEMM_OK;
@@ -342,8 +371,11 @@ template <class I, class V> struct Engine : EngineBase {
                                        &ps.pcnt, nullptr, ps.sym_hist, st));
         ps.nheavy = 0;
         for (int t = kHeavyTier0; t < kTiers; ++t) ps.nheavy += ps.sym_hist[t];
+        int tsc = cx.tbegin(kPhScan, st);
         SPG_CK(exclusive_scan_i64(ps.cnt.as<int64_t>(), n, ps.colptr.as<int64_t>(),
                                   ps.scan_part.as<int64_t>(), 1, st));
+        cx.tend(tsc, st);
+        cx.launched(3);
         // k-split stages: per-stage counts nnz(D_t(:, j)) (LocalSymbolic per stage,
         // Algorithm 3), panel counts for the heavy columns
         if (ps.s > 1) {
@@ -361,6 +393,7 @@ template <class I, class V> struct Engine : EngineBase {
                                                nullptr, st));
                 SPG_CK(exclusive_scan_i64(scnt, n, ps.stage_colptr.as<int64_t>() + (size_t)t * (n + 1),
                                           ps.scan_part.as<int64_t>(), 1, st));
+                cx.launched(3);
             }
             SPG_CK(cudaMemcpyAsync(ps.h_stage_colptr.p, ps.stage_colptr.p,
                                    sizeof(int64_t) * (size_t)ps.s * (n + 1), cudaMemcpyDeviceToHost, st));
@@ -368,8 +401,11 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(cudaMemcpyAsync(ps.h_colptr.p, ps.colptr.p, sizeof(int64_t) * (n + 1),
                                cudaMemcpyDeviceToHost, st));
         SPG_CK(cudaMemcpyAsync(ps.h_small.as<char>() + 256, ps.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        tsc = cx.tbegin(kPhScan, st);
         SPG_CK(exclusive_scan_i64(ps.f.as<int64_t>(), n, ps.wbytes.as<int64_t>(),
                                   ps.scan_part.as<int64_t>(), 1, st));
+        cx.tend(tsc, st);
+        cx.launched(3);
         SPG_CK(cudaMemcpyAsync(ps.h_small.as<char>() + 512, ps.wbytes.as<int64_t>() + n, sizeof(int64_t),
                                cudaMemcpyDeviceToHost, st));
         if (ps.nheavy) SPG_ST(build_panels(ps, st));
@@ -395,6 +431,7 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(ps.ap_row.ensure(sizeof(uint16_t) * (nnzA + 8)));
         SPG_CK(ps.ap_val.ensure(sizeof(V) * (nnzA + 8)));
         SPG_CK(ps.merge_tmp.ensure(sizeof(int64_t) * scan_partials_len(N + 1)));
+        const int tp = ps.timer.begin(kPhPanels, st);
         SPG_CK(cudaMemsetAsync(ps.ap_end.p, 0, sizeof(int64_t) * (N + 1), st));
         const int blocks = ps.nsm * 8;
         k_panel_count<I><<<blocks, 256, 0, st>>>((const I *)ps.A.colptr, (const I *)ps.A.rowidx, ka,
@@ -405,6 +442,8 @@ template <class I, class V> struct Engine : EngineBase {
                                                       (const V *)ps.A.vals, ka, ps.tun.log2R,
                                                       ps.ap_end.as<unsigned long long>(),
                                                       ps.ap_row.as<uint16_t>(), ps.ap_val.as<V>());
+        ps.timer.end(tp, st);
+        ps.timer.launches += 5;
         SPG_CK(cudaGetLastError());
         ps.panels_built = true;
         return SPGEMM_OK;
@@ -568,6 +607,8 @@ template <class I, class V> struct Engine : EngineBase {
                     ps.off_num.as<int32_t>(), st)));
             }
             // sort-free hash merge of the stage partials (Sec. IV-D)
+            cx.ph_hash = kPhMerge;
+            cx.ph_dense = kPhMerge;
             PA pa{ps.parts_tab.as<PartDev<I, V>>() + (size_t)t * ps.s, ps.s, ps.m};
             NumOut<I, V> o{ps.colptr.as<int64_t>(), hc[b.c0], (I *)C->rowidx, (V *)C->vals};
             SPG_ST((num_pass<SrcParts<I, V>, SrcPartsPanel<I, V>>(
@@ -578,6 +619,7 @@ template <class I, class V> struct Engine : EngineBase {
         }
         SPG_CK(rebase_colptr(ps.colptr.as<int64_t>() + b.c0, b.c1 - b.c0, C->colptr,
                              C->ptr_type == SPGEMM_I64, st));
+        cx.launched();
         return SPGEMM_OK;
     }
 
@@ -598,11 +640,13 @@ template <class I, class V> struct Engine : EngineBase {
         ga.gvals = (const V *)G->vals;
         ga.dA = (V *)dA;
         ga.dB = (V *)dB;
+        const int tbw = cx.tbegin(kPhBackward, st);
         if (ps.A.nnz)
             k_fill_zero<V><<<(unsigned)((ps.A.nnz + 255) / 256), 256, 0, st>>>((V *)dA, ps.A.nnz);
         if (ps.B.nnz)
             k_fill_zero<V><<<(unsigned)((ps.B.nnz + 255) / 256), 256, 0, st>>>((V *)dB, ps.B.nnz);
-        if (n == 0) return SPGEMM_OK;
+        cx.launched(2);
+        if (n == 0) { cx.tend(tbw, st); return SPGEMM_OK; }
         SPG_CK(cudaMemsetAsync(cx.hist, 0, sizeof(int32_t) * 64, st));
         SPG_CK(cudaMemsetAsync(cx.cursor, 0, sizeof(int32_t) * 64, st));
         k_bwd_tier<I, V><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ga, n, cx.tun.hash_cap_max,
@@ -629,7 +673,7 @@ template <class I, class V> struct Engine : EngineBase {
             }
             const int thr = block_tier_threads(T, cx.tun);
             const int smem = T * (int)(4 + sizeof(V));
-            const int per_sm = std::max(1, std::min(2048 / thr, (220 * 1024) / smem));
+            const int per_sm = std::max(1, std::min(2048 / thr, (228 * 1024) / (smem + 34 * 1024)));
             const int blocks = std::max(1, std::min(hist[t], cx.nsm * per_sm));
             switch (T) {
                 case 512: k_bwd_block<I, V, 512><<<blocks, thr, smem, st>>>(ga, c); break;
@@ -645,7 +689,11 @@ template <class I, class V> struct Engine : EngineBase {
         if (nheavy) {
             const int smem = dense_smem(cx);
             k_bwd_dense<I, V><<<cx.nsm, 1024, smem, st>>>(ga, c);
+            cx.launched();
         }
+        for (int t = 1; t <= 8; ++t) if (hist[t]) cx.launched();
+        cx.launched(2);
+        cx.tend(tbw, st);
         SPG_CK(cudaGetLastError());
         return SPGEMM_OK;
     }
@@ -660,10 +708,10 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(cudaGetDeviceProperties(&prop, dev));
         PlanState tmp;   // scratch only
         tmp.nsm = prop.multiProcessorCount;
-        tmp.tun.log2R = sizeof(V) == 4 ? 15 : 14;
+        tmp.tun.log2R = sizeof(V) == 4 ? 14 : 13;
         const int64_t R = 1ll << tmp.tun.log2R;
         tmp.P = (int)std::max<int64_t>(1, (m + R - 1) / R);
-        const int64_t maxbm = (int64_t)(192 * 1024) * 8;
+        const int64_t maxbm = (int64_t)(160 * 1024) * 8;
         const int64_t mpad = ((m + R - 1) / R) * R;
         tmp.Rs = mpad <= maxbm ? (mpad > 0 ? mpad : R) : (maxbm / R) * R;
         tmp.Q = (int)std::max<int64_t>(1, (m + tmp.Rs - 1) / tmp.Rs);

@@ -281,25 +281,37 @@ __device__ __forceinline__ void warp_walk(int64_t beg, int len, V bv, int64_t ta
     }
 }
 
-template <class V> struct HugeSeg { int64_t beg; int64_t tag; V bv; int len; };
+constexpr int kMaxBlock = 1024;
 
-constexpr int kHugeQ = 32;
-
+// Per-CTA scratch of the load-balanced walk: the non-empty segments of the
+// current chunk, compacted, with their start in the flattened product stream.
 template <class V> struct BlockShared {
-    HugeSeg<V> hq[kHugeQ];
-    int hq_n;
+    int64_t start[kMaxBlock + 1];
+    int64_t qb[kMaxBlock];     // beg - start: entry index = qb[s] + stream position
+    int64_t tag[kMaxBlock];
+    V bv[kMaxBlock];
+    int64_t red64[33];
+    int nz;
     int pos;
     unsigned long long tot;
     int red[32];
 };
 
-// Block-level walk over the segments of src. Segments longer than huge_seg
-// are queued and walked by the whole CTA. All threads must call it; it ends
-// with a __syncthreads.
+// Block-level load-balanced walk over the segments of src. emit(q, bv, tag,
+// valid) is called by all 32 lanes of a warp together (warp-synchronous
+// emits may use warp intrinsics); lanes with valid == false carry no entry. Each chunk of
+// blockDim segments is compacted to its non-empty segments and prefix-summed
+// into a flattened product stream [0, T); every warp takes an equal
+// contiguous share of the stream in 32-wide windows, and lane l of a window
+// finds its segment from a bitmask of the segment starts inside the window.
+// Consecutive lanes read consecutive entries of a segment (coalesced). All
+// threads must call it; it ends with a __syncthreads.
 template <class Src, class Emit>
-__device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short_seg, int huge_seg,
+__device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int, int,
                                            BlockShared<typename Src::Val> &sh) {
     using V = typename Src::Val;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
     const int64_t nseg = src.nseg();
     for (int64_t base = 0; base < nseg; base += blockDim.x) {
         const int64_t e = base + threadIdx.x;
@@ -307,24 +319,64 @@ __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short
         int len = 0;
         V bv = V(0);
         if (e < nseg) src.seg(e, beg, len, bv, tag);
-        if (len > huge_seg) {
-            const int slot = atomicAdd(&sh.hq_n, 1);
-            if (slot < kHugeQ) {
-                sh.hq[slot].beg = beg; sh.hq[slot].len = len; sh.hq[slot].bv = bv;
-                sh.hq[slot].tag = tag;
-                len = 0;
+        // block scan of (nonempty << 40 | len): compacted slot and stream start
+        const int64_t key = ((int64_t)(len > 0) << 40) | (int64_t)len;
+        int64_t incl = warp_incl_scan(key);
+        if (lane == 31) sh.red64[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = lane < nw ? sh.red64[lane] : 0;
+            int64_t wi = warp_incl_scan(w);
+            sh.red64[lane] = wi - w;
+            if (lane == 31) sh.red64[32] = wi;
+        }
+        __syncthreads();
+        const int64_t ex = sh.red64[warp] + incl - key;
+        if (len > 0) {
+            const int slot = (int)(ex >> 40);
+            const int64_t st0 = ex & ((1ll << 40) - 1);
+            sh.start[slot] = st0;
+            sh.qb[slot] = beg - st0;
+            sh.bv[slot] = bv;
+            sh.tag[slot] = tag;
+        }
+        const int64_t tot = sh.red64[32];
+        const int nz = (int)(tot >> 40);
+        const int64_t T = tot & ((1ll << 40) - 1);
+        __syncthreads();   // (start[nz] is never read: lookups stop at nz - 1)
+        if (T > 0) {
+            // this warp's share of [0, T), in whole windows
+            const int64_t nwin = (T + 31) >> 5;
+            const int64_t per = (nwin + nw - 1) / nw;
+            const int64_t p0 = (int64_t)warp * per * 32;
+            int64_t p1 = p0 + per * 32;
+            if (p1 > T) p1 = T;
+            if (p0 < p1) {
+                // last segment starting at or before p0
+                int lo = 0, hi = nz - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sh.start[mid] <= p0) lo = mid; else hi = mid - 1;
+                }
+                int s_lo = lo;
+                for (int64_t wb = p0; wb < p1; wb += 32) {
+                    const int j = s_lo + 1 + lane;
+                    unsigned bit = 0u;
+                    if (j < nz) {
+                        const int64_t sj = sh.start[j];
+                        if (sj < wb + 32) bit = 1u << (int)(sj - wb);
+                    }
+                    const unsigned M = __reduce_or_sync(SPG_FULL, bit);
+                    const int sg = s_lo + __popc(M & (0xffffffffu >> (31 - lane)));
+                    const int64_t t = wb + lane;
+                    const bool valid = t < p1;
+                    const int sgv = valid ? sg : s_lo;
+                    emit(sh.qb[sgv] + (valid ? t : sh.start[sgv]), sh.bv[sgv], sh.tag[sgv], valid);
+                    s_lo += __popc(M);
+                    if (s_lo + 1 < nz && sh.start[s_lo + 1] == wb + 32) ++s_lo;
+                }
             }
         }
-        warp_walk(beg, len, bv, tag, short_seg, emit);
-        __syncthreads();
-        int nh = sh.hq_n;
-        if (nh > kHugeQ) nh = kHugeQ;
-        for (int h = 0; h < nh; ++h) {
-            const HugeSeg<V> s = sh.hq[h];
-            for (int i = threadIdx.x; i < s.len; i += blockDim.x) emit(s.beg + i, s.bv, s.tag);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) sh.hq_n = 0;
         __syncthreads();
     }
 }
@@ -486,7 +538,6 @@ __global__ void k_sym_block(typename Src::Args sa, TierCommon c) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *keys = reinterpret_cast<uint32_t *>(smem);
     __shared__ BlockShared<V> sh;
-    if (threadIdx.x == 0) sh.hq_n = 0;
     const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
     for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {
         const int64_t g = c.list[it];
@@ -495,7 +546,8 @@ __global__ void k_sym_block(typename Src::Args sa, TierCommon c) {
         for (int s = threadIdx.x; s < T; s += blockDim.x) keys[s] = kEmpty;
         __syncthreads();
         int mine = 0;
-        auto emit = [&](int64_t q, V, int64_t) {
+        auto emit = [&](int64_t q, V, int64_t, bool valid) {
+            if (!valid) return;
             bool nw;
             hash_insert(keys, LOG2T, src.row(q), nw, c.err);
             mine += nw;
@@ -517,14 +569,14 @@ __global__ void k_sym_block(typename Src::Args sa, TierCommon c) {
 // panel q, heavy column), largest heavy sub-tier first. Writes per numeric
 // panel counts pcnt[h*P + p] and adds the column total to cnt[g].
 template <class Src>
-__global__ void __launch_bounds__(1024) k_sym_bitmap(typename Src::Args sa, TierCommon c) {
+__global__ void __launch_bounds__(1024, 1) k_sym_bitmap(typename Src::Args sa, TierCommon c) {
     using V = typename Src::Val;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *bm = reinterpret_cast<uint32_t *>(smem);
     __shared__ BlockShared<V> sh;
     const int nwords_max = (int)((c.Rs + 31) >> 5);
     for (int w = threadIdx.x; w < nwords_max; w += blockDim.x) bm[w] = 0u;
-    if (threadIdx.x == 0) { sh.hq_n = 0; sh.tot = 0; }
+    if (threadIdx.x == 0) { sh.tot = 0; }
     __syncthreads();
     const int lo = c.list_off[kHeavyTier0], hi = c.list_off[kTiers];
     const int64_t nitems = (int64_t)(hi - lo) * c.Q;
@@ -542,7 +594,8 @@ __global__ void __launch_bounds__(1024) k_sym_bitmap(typename Src::Args sa, Tier
         const int64_t rows = (mrows - r0) < c.Rs ? (mrows - r0) : c.Rs;
         const int nwords = (int)((rows + 31) >> 5);
         const bool filt = c.Q > 1;
-        auto emit = [&](int64_t qq, V, int64_t) {
+        auto emit = [&](int64_t qq, V, int64_t, bool valid) {
+            if (!valid) return;
             int64_t r = (int64_t)src.row(qq);
             if (filt) {
                 r -= r0;
@@ -637,7 +690,7 @@ __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::I
     V *vals = reinterpret_cast<V *>(smem);
     uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * T);
     __shared__ BlockShared<V> sh;
-    if (threadIdx.x == 0) { sh.hq_n = 0; sh.pos = 0; }
+    if (threadIdx.x == 0) { sh.pos = 0; }
     const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
     const int lane = threadIdx.x & 31;
     for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {
@@ -646,7 +699,8 @@ __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::I
         src.open(sa, g);
         for (int s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = kEmpty; vals[s] = V(0); }
         __syncthreads();
-        auto emit = [&](int64_t q, V bv, int64_t) {
+        auto emit = [&](int64_t q, V bv, int64_t, bool valid) {
+            if (!valid) return;
             bool nw;
             const int h = hash_insert(keys, LOG2T, src.row(q), nw, c.err);
             if (h >= 0) atomic_add_v(&vals[h], src.val(q, bv));
@@ -685,7 +739,7 @@ __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::I
 // pcnt_in[h*P+p] entries at the column's offset plus the counts of the lower
 // panels (rows grouped by panel, ascending within the panel).
 template <class DSrc>
-__global__ void __launch_bounds__(1024) k_num_dense(typename DSrc::Args sa, TierCommon c,
+__global__ void __launch_bounds__(512, 2) k_num_dense(typename DSrc::Args sa, TierCommon c,
                                                     typename DSrc::Idx *out_rows,
                                                     typename DSrc::Val *out_vals) {
     using V = typename DSrc::Val;
@@ -693,11 +747,12 @@ __global__ void __launch_bounds__(1024) k_num_dense(typename DSrc::Args sa, Tier
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = 1 << c.log2R;
     V *acc = reinterpret_cast<V *>(smem);
-    uint32_t *bm = reinterpret_cast<uint32_t *>(smem + sizeof(V) * R);
+    // presence flags: one byte per row, set with plain stores (no read-modify-write)
+    unsigned char *flg = smem + sizeof(V) * R;
+    uint32_t *flg4 = reinterpret_cast<uint32_t *>(flg);
     __shared__ BlockShared<V> sh;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) acc[r] = V(0);
-    for (int w = threadIdx.x; w < (R >> 5); w += blockDim.x) bm[w] = 0u;
-    if (threadIdx.x == 0) { sh.hq_n = 0; sh.pos = 0; }
+    for (int r = threadIdx.x; r < R; r += blockDim.x) { acc[r] = V(0); flg[r] = 0; }
+    if (threadIdx.x == 0) sh.pos = 0;
     __syncthreads();
     const int lo = c.list_off[kHeavyTier0], hi = c.list_off[kTiers];
     const int nh = hi - lo;
@@ -719,37 +774,39 @@ __global__ void __launch_bounds__(1024) k_num_dense(typename DSrc::Args sa, Tier
         const int64_t out0 = c.colptr[g] - c.out_base + below;
         DSrc src;
         src.open(sa, c, g, p, h);
-        auto emit = [&](int64_t q, V bv, int64_t) {
+        auto emit = [&](int64_t q, V bv, int64_t, bool valid) {
+            if (!valid) return;
             const int r = src.lrow(q);
             if (r < 0) return;
             atomic_add_v(&acc[r], src.val(q, bv));
-            atomicOr(&bm[r >> 5], 1u << (r & 31));
+            flg[r] = 1;
         };
         block_walk(src, emit, c.short_seg, c.huge_seg, sh);
-        // compaction: each thread takes bitmap words; warp-aggregated slots
+        // compaction: each thread takes 4-row flag words; warp-aggregated slots
         const int64_t rbase = (int64_t)p << c.log2R;
-        for (int w0 = 0; w0 < (R >> 5); w0 += blockDim.x) {
+        for (int w0 = 0; w0 < (R >> 2); w0 += blockDim.x) {
             const int w = w0 + threadIdx.x;
-            uint32_t x = w < (R >> 5) ? bm[w] : 0u;
-            const int n1 = __popc(x);
+            const uint32_t x = w < (R >> 2) ? flg4[w] : 0u;
+            const int n1 = __popc(x);   // flags are 0 or 1 per byte
             const int incl = warp_incl_scan(n1);
             const int tot = __shfl_sync(SPG_FULL, incl, 31);
             int wb = 0;
             if (lane == 31 && tot) wb = atomicAdd(&sh.pos, tot);
             wb = __shfl_sync(SPG_FULL, wb, 31);
             if (x) {
-                bm[w] = 0u;
+                flg4[w] = 0u;
                 int o = wb + incl - n1;
-                while (x) {
-                    const int bit = __ffs(x) - 1;
-                    x &= x - 1;
-                    const int r = w * 32 + bit;
-                    if (o < mycnt) {
-                        out_rows[out0 + o] = (I)(rbase + r);
-                        out_vals[out0 + o] = acc[r];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    if ((x >> (8 * b)) & 1u) {
+                        const int r = w * 4 + b;
+                        if (o < mycnt) {
+                            out_rows[out0 + o] = (I)(rbase + r);
+                            out_vals[out0 + o] = acc[r];
+                        }
+                        acc[r] = V(0);
+                        ++o;
                     }
-                    acc[r] = V(0);
-                    ++o;
                 }
             }
         }
@@ -838,7 +895,6 @@ __global__ void k_bwd_block(GradArgs<I, V> a, TierCommon c) {
     V *gv = reinterpret_cast<V *>(smem);
     uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * T);
     __shared__ BlockShared<V> sh;
-    if (threadIdx.x == 0) sh.hq_n = 0;
     const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
     for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {
         const int64_t g = c.list[it];
@@ -854,7 +910,8 @@ __global__ void k_bwd_block(GradArgs<I, V> a, TierCommon c) {
         __syncthreads();
         SrcGemm<I, V> src;
         src.open(a.gemm, g);
-        auto emit = [&](int64_t q, V bv, int64_t pe) {
+        auto emit = [&](int64_t q, V bv, int64_t pe, bool valid) {
+            if (!valid) return;
             const int h = hash_find(keys, LOG2T, src.row(q));
             if (h < 0) return;
             const V gval = gv[h];
@@ -913,7 +970,7 @@ __global__ void __launch_bounds__(1024) k_bwd_dense(GradArgs<I, V> a, TierCommon
     __shared__ BlockShared<V> sh;
     __shared__ int s_any;
     for (int w = threadIdx.x; w < (R >> 5); w += blockDim.x) bm[w] = 0u;
-    if (threadIdx.x == 0) { sh.hq_n = 0; s_any = 0; }
+    if (threadIdx.x == 0) { s_any = 0; }
     __syncthreads();
     const int lo = c.list_off[kHeavyTier0], hi = c.list_off[kTiers];
     const int nh = hi - lo;
@@ -936,7 +993,8 @@ __global__ void __launch_bounds__(1024) k_bwd_dense(GradArgs<I, V> a, TierCommon
         if (s_any) {
             SrcGemm<I, V> src;
             src.open(a.gemm, g);
-            auto emit = [&](int64_t q, V bv, int64_t pe) {
+            auto emit = [&](int64_t q, V bv, int64_t pe, bool valid) {
+                if (!valid) return;
                 const int64_t r = (int64_t)src.row(q) - r0;
                 if (r < 0 || r >= R) return;
                 if (!((bm[r >> 5] >> (r & 31)) & 1u)) return;

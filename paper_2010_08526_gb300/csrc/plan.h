@@ -62,6 +62,63 @@ struct Batch {
     std::vector<int64_t> doff;  // offset of stage t's partials in the partial buffer
 };
 
+// Per-phase device time (CUDA events on the launching stream) and kernel
+// launch counts of a plan.
+enum Phase : int {
+    kPhFlopsBin = 0, kPhSymHash = 1, kPhSymHeavy = 2, kPhScan = 3, kPhPanels = 4,
+    kPhNumHash = 5, kPhNumDense = 6, kPhMerge = 7, kPhBackward = 8, kNumPhases = 9
+};
+
+struct PhaseTimer {
+    bool enabled = false;
+    struct Rec { int phase; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double ms[kNumPhases] = {0};
+    int64_t count[kNumPhases] = {0};
+    int64_t launches = 0;
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    int begin(int phase, cudaStream_t st) {
+        if (!enabled) return -1;
+        Rec r{phase, get(), get()};
+        cudaEventRecord(r.a, st);
+        recs.push_back(r);
+        return (int)recs.size() - 1;
+    }
+    void end(int idx, cudaStream_t st) {
+        if (idx < 0) return;
+        cudaEventRecord(recs[(size_t)idx].b, st);
+    }
+    void collect() {
+        for (auto &r : recs) {
+            float t = 0.f;
+            cudaEventSynchronize(r.b);
+            if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+                ms[r.phase] += t;
+                count[r.phase] += 1;
+            }
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+    }
+    void reset() {
+        collect();
+        for (int i = 0; i < kNumPhases; ++i) { ms[i] = 0; count[i] = 0; }
+        launches = 0;
+    }
+    void release() {
+        collect();
+        for (auto e : pool) cudaEventDestroy(e);
+        pool.clear();
+    }
+};
+
 struct EngineBase;
 
 struct PlanState {
@@ -84,6 +141,8 @@ struct PlanState {
     HostBuf h_colptr, h_small, h_stage_colptr, h_parts;
     std::vector<DevBuf> ring_col, ring_row, ring_val;   // spgemm_run_batched device ring
     std::vector<HostBuf> host_slots;                     // spgemm_run_batched pinned slots
+
+    PhaseTimer timer;
 
     // symbolic results
     bool have_symbolic = false;

@@ -319,6 +319,7 @@ def test_backward_matches_oracle():
     A, B = W.config5(m=3000, k=3000, n=1500, value_dtype=np.float64)
     C = oracle.spgemm(A, B)
     G = shuffle_within_columns(W.values_on_pattern(C, 17, dist="normal", value_dtype=np.float64), 5)
+    G = G.astype(index_dtype=np.int32)
     dA, dB = spg.backward(to_dev(A), to_dev(B), to_dev(G))
     torch.cuda.synchronize()
     rA, rB = oracle.backward(A, B, G)
@@ -330,7 +331,7 @@ def test_backward_heavy_columns():
     A = skewed(4000, 3000, 121, hubs=2, hub_deg=2000)
     B = skewed(3000, 200, 122, hubs=1, hub_deg=2500)
     C = oracle.spgemm(A, B)
-    G = W.values_on_pattern(C, 18, dist="normal", value_dtype=np.float64)
+    G = W.values_on_pattern(C, 18, dist="normal", value_dtype=np.float64).astype(index_dtype=np.int32)
     Ad, Bd = to_dev(A), to_dev(B)
     plan = spg.Plan(Ad, Bd, tuning=spg.Tuning(hash_max_cap=256, panel_rows=1024))
     dA, dB = plan.backward(to_dev(G))
@@ -339,6 +340,14 @@ def test_backward_heavy_columns():
     np.testing.assert_allclose(dA.cpu().numpy(), rA, rtol=1e-10, atol=1e-10)
     np.testing.assert_allclose(dB.cpu().numpy(), rB, rtol=1e-10, atol=1e-10)
     plan.close()
+
+
+def test_backward_rejects_mismatched_g():
+    A, B = W.config5(m=300, k=300, n=200, value_dtype=np.float64)
+    C = oracle.spgemm(A, B)      # int64 indices
+    G = W.values_on_pattern(C, 3, dist="normal", value_dtype=np.float64)
+    with pytest.raises(spg.SpgemmError):
+        spg.backward(to_dev(A), to_dev(B), to_dev(G))
 
 
 def test_autograd_function_fp64_finite_differences():
