@@ -23,7 +23,8 @@ size_t PlanState::workspace_bytes() const {
     const DevBuf *bufs[] = {&probs, &f, &cnt, &colptr, &tier, &list_sym, &list_num, &hist, &cursor,
                             &off_sym, &off_num, &heavy_ord, &pcnt, &err, &scan_part, &wbytes,
                             &valid_flag, &ap_end, &ap_row, &ap_val, &stage_cnt, &stage_colptr,
-                            &stage_pcnt, &merge_tmp, &drows, &dvals, &parts_tab};
+                            &stage_pcnt, &merge_tmp, &drows, &dvals, &parts_tab, &items, &item_cnt,
+                            &item_off};
     size_t s = 0;
     for (auto *b : bufs) s += b->bytes;
     return s;
@@ -33,7 +34,8 @@ void PlanState::release_all() {
     DevBuf *bufs[] = {&probs, &f, &cnt, &colptr, &tier, &list_sym, &list_num, &hist, &cursor,
                       &off_sym, &off_num, &heavy_ord, &pcnt, &err, &scan_part, &wbytes,
                       &valid_flag, &ap_end, &ap_row, &ap_val, &stage_cnt, &stage_colptr,
-                      &stage_pcnt, &merge_tmp, &drows, &dvals, &parts_tab};
+                      &stage_pcnt, &merge_tmp, &drows, &dvals, &parts_tab, &items, &item_cnt,
+                      &item_off};
     for (auto *b : bufs) b->release();
     h_colptr.release();
     h_small.release();

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <array>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -137,6 +138,8 @@ template <class I, class V> struct Engine : EngineBase {
         set_smem(k_num_dense<SrcPanel<I, V>>, mx);
         set_smem(k_num_dense<SrcPartsPanel<I, V>>, mx);
         set_smem(k_bwd_dense<I, V>, mx);
+        set_smem(k_num_heavy<SrcPanelRange<I, V>>, mx);
+        set_smem(k_num_heavy<SrcPartsRange<I, V>>, mx);
         (void)sv;
         done = true;
     }
@@ -202,6 +205,45 @@ template <class I, class V> struct Engine : EngineBase {
         return R * (int)sizeof(V) + R;
     }
 
+    static int heavy_smem(const Ctx &cx) {
+        const int hs = (1 << kRangeLog2T) * (int)(sizeof(V) + 4);
+        return std::max(dense_smem(cx), hs);
+    }
+
+    // Cut the heavy columns of the symbolic list into work items (dense
+    // panels and hash ranges) from their per-panel output counts; reads the
+    // item total back (one small synchronisation).
+    static spgemm_status build_items(const Ctx &cx, int nheavy, const int32_t *sym_list,
+                                     const int32_t *sym_off, const int64_t *sel,
+                                     const int32_t *pcnt, int64_t n, DevBuf &items, DevBuf &icnt,
+                                     DevBuf &ioff, DevBuf &scan_part, int64_t *n_items,
+                                     cudaStream_t st) {
+        *n_items = 0;
+        if (!nheavy) return SPGEMM_OK;
+        SPG_CK(icnt.ensure(sizeof(int64_t) * (nheavy + 1)));
+        SPG_CK(ioff.ensure(sizeof(int64_t) * (nheavy + 1)));
+        SPG_CK(scan_part.ensure(sizeof(int64_t) * scan_partials_len(std::max<int64_t>(n, nheavy) + 1)));
+        const int R = 1 << cx.tun.log2R;
+        const int dmin = std::max(1, R / 8);
+        const unsigned nb = (unsigned)((nheavy + 255) / 256);
+        k_heavy_items<<<nb, 256, 0, st>>>(sym_list, sym_off, sel, cx.tun.hash_cap_max, 0, n, pcnt, cx.P,
+                                          dmin, 0, icnt.as<int64_t>(), nullptr, nullptr);
+        SPG_CK(exclusive_scan_i64(icnt.as<int64_t>(), nheavy, ioff.as<int64_t>(),
+                                  scan_part.as<int64_t>(), 1, st));
+        int64_t total = 0;
+        SPG_CK(cudaMemcpyAsync(cx.h_small + 256, ioff.as<int64_t>() + nheavy, sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        std::memcpy(&total, cx.h_small + 256, sizeof(int64_t));
+        SPG_CK(items.ensure(sizeof(HeavyItem) * (size_t)(total + 1)));
+        k_heavy_items<<<nb, 256, 0, st>>>(sym_list, sym_off, sel, cx.tun.hash_cap_max, 0, n, pcnt, cx.P,
+                                          dmin, 1, nullptr, ioff.as<int64_t>(), items.as<HeavyItem>());
+        cx.launched(5);
+        SPG_CK(cudaGetLastError());
+        *n_items = total;
+        return SPGEMM_OK;
+    }
+
     // ---- symbolic pass -------------------------------------------------------
     // Bins columns [c_lo, c_hi) of the source, counts distinct rows into
     // cnt_out, fills list/off; heavy columns get per-panel counts in pcnt.
@@ -262,14 +304,15 @@ template <class I, class V> struct Engine : EngineBase {
     // ---- numeric pass --------------------------------------------------------
     // tc: host tier populations (nullptr: device-driven grids). heavy: whether
     // dense items exist. sym_list/sym_off: the symbolic heavy list.
-    template <class Src, class DSrc>
+    template <class Src, class DSrc, class RSrc = DSrc>
     static spgemm_status num_pass(const Ctx &cx, const typename Src::Args &sa,
                            const typename DSrc::Args &da, int64_t c_lo, int64_t c_hi,
                            const int64_t *cnt, const int64_t *dense_sel, const NumOut<I, V> &o,
                            const int *tc, bool heavy, const int32_t *sym_list,
                            const int32_t *sym_off, const int32_t *heavy_ord,
                            const int32_t *pcnt_in, uint8_t *tier, int32_t *list, int32_t *off,
-                           cudaStream_t st) {
+                           cudaStream_t st, const HeavyItem *items = nullptr,
+                           const int64_t *n_items_dev = nullptr, int64_t n_items = 0) {
         const int64_t nc = c_hi - c_lo;
         bool any_hash = tc == nullptr;
         if (tc) for (int t = 1; t <= 8; ++t) any_hash |= tc[t] > 0;
@@ -300,11 +343,26 @@ template <class I, class V> struct Engine : EngineBase {
             c.heavy_ord = heavy_ord;
             c.pcnt_in = pcnt_in;
             c.c_lo = c_lo; c.c_hi = c_hi;
-            const int smem = dense_smem(cx);
-            const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 34 * 1024)));
-            const int td = cx.tbegin(cx.ph_dense, st);
-            k_num_dense<DSrc><<<cx.nsm * per_sm, 512, smem, st>>>(da, c, o.rows, o.vals);
-            cx.tend(td, st);
+            if constexpr (!std::is_same<RSrc, DSrc>::value) {
+              if (items) {
+                const int smem = heavy_smem(cx);
+                const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 34 * 1024)));
+                const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * per_sm));
+                const int td = cx.tbegin(cx.ph_dense, st);
+                k_num_heavy<RSrc><<<blocks, 512, smem, st>>>(da, c, items, n_items_dev, o.rows, o.vals);
+                cx.tend(td, st);
+                cx.launched();
+                SPG_CK(cudaGetLastError());
+                return SPGEMM_OK;
+              }
+            }
+            {
+                const int smem = dense_smem(cx);
+                const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 34 * 1024)));
+                const int td = cx.tbegin(cx.ph_dense, st);
+                k_num_dense<DSrc><<<cx.nsm * per_sm, 512, smem, st>>>(da, c, o.rows, o.vals);
+                cx.tend(td, st);
+            }
             cx.launched();
         }
         SPG_CK(cudaGetLastError());
@@ -409,6 +467,9 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(cudaMemcpyAsync(ps.h_small.as<char>() + 512, ps.wbytes.as<int64_t>() + n, sizeof(int64_t),
                                cudaMemcpyDeviceToHost, st));
         if (ps.nheavy) SPG_ST(build_panels(ps, st));
+        SPG_ST(build_items(cx, ps.nheavy, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
+                           ps.cnt.as<int64_t>(), ps.pcnt.as<int32_t>(), n, ps.items, ps.item_cnt,
+                           ps.item_off, ps.scan_part, &ps.n_items, st));
         SPG_CK(cudaStreamSynchronize(st));
         const int errw = *(int *)(ps.h_small.as<char>() + 256);
         if (errw) {
@@ -584,11 +645,12 @@ template <class I, class V> struct Engine : EngineBase {
         if (ps.s == 1) {
             NumOut<I, V> o{ps.colptr.as<int64_t>(), hc[b.c0], (I *)C->rowidx, (V *)C->vals};
             GA ga = gemm_args(ps, 0, ps.k);
-            SPG_ST((num_pass<SrcGemm<I, V>, SrcPanel<I, V>>(
+            SPG_ST((num_pass<SrcGemm<I, V>, SrcPanel<I, V>, SrcPanelRange<I, V>>(
                 cx, ga, ga, b.c0, b.c1, ps.cnt.as<int64_t>(), ps.cnt.as<int64_t>(), o, b.tc[0].data(),
                 b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                 ps.heavy_ord.as<int32_t>(), ps.pcnt.as<int32_t>(), ps.tier.as<uint8_t>(),
-                ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st)));
+                ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
+                ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items)));
         } else {
             const int64_t *hs = ps.h_stage_colptr.as<int64_t>();
             for (int s = 0; s < ps.s; ++s) {
@@ -611,11 +673,12 @@ template <class I, class V> struct Engine : EngineBase {
             cx.ph_dense = kPhMerge;
             PA pa{ps.parts_tab.as<PartDev<I, V>>() + (size_t)t * ps.s, ps.s, ps.m};
             NumOut<I, V> o{ps.colptr.as<int64_t>(), hc[b.c0], (I *)C->rowidx, (V *)C->vals};
-            SPG_ST((num_pass<SrcParts<I, V>, SrcPartsPanel<I, V>>(
+            SPG_ST((num_pass<SrcParts<I, V>, SrcPartsPanel<I, V>, SrcPartsRange<I, V>>(
                 cx, pa, pa, b.c0, b.c1, ps.cnt.as<int64_t>(), ps.cnt.as<int64_t>(), o, b.tc[0].data(),
                 b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                 ps.heavy_ord.as<int32_t>(), ps.pcnt.as<int32_t>(), ps.tier.as<uint8_t>(),
-                ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st)));
+                ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
+                ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items)));
         }
         SPG_CK(rebase_colptr(ps.colptr.as<int64_t>() + b.c0, b.c1 - b.c0, C->colptr,
                              C->ptr_type == SPGEMM_I64, st));
@@ -770,12 +833,17 @@ template <class I, class V> struct Engine : EngineBase {
         }
         int nheavy = 0;
         for (int t = kHeavyTier0; t < kTiers; ++t) nheavy += hist[t];
+        int64_t n_items = 0;
+        SPG_ST(build_items(cx, nheavy, tmp.list_sym.as<int32_t>(), tmp.off_sym.as<int32_t>(),
+                           tmp.cnt.as<int64_t>(), tmp.pcnt.as<int32_t>(), n, tmp.items, tmp.item_cnt,
+                           tmp.item_off, tmp.scan_part, &n_items, st));
         NumOut<I, V> o{tmp.colptr.as<int64_t>(), 0, (I *)out->rowidx, (V *)out->vals};
-        SPG_ST((num_pass<SrcParts<I, V>, SrcPartsPanel<I, V>>(
+        SPG_ST((num_pass<SrcParts<I, V>, SrcPartsPanel<I, V>, SrcPartsRange<I, V>>(
             cx, pa, pa, 0, n, tmp.cnt.as<int64_t>(), tmp.cnt.as<int64_t>(), o, nullptr, nheavy > 0,
             tmp.list_sym.as<int32_t>(), tmp.off_sym.as<int32_t>(), tmp.heavy_ord.as<int32_t>(),
             tmp.pcnt.as<int32_t>(), tmp.tier.as<uint8_t>(), tmp.list_num.as<int32_t>(),
-            tmp.off_num.as<int32_t>(), st)));
+            tmp.off_num.as<int32_t>(), st, tmp.items.as<HeavyItem>(),
+            tmp.item_off.as<int64_t>() + nheavy, n_items)));
         int errw = 0;
         SPG_CK(cudaMemcpyAsync(&errw, tmp.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         SPG_CK(cudaStreamSynchronize(st));

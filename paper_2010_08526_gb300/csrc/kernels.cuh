@@ -359,21 +359,41 @@ __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int, int,
                     if (sh.start[mid] <= p0) lo = mid; else hi = mid - 1;
                 }
                 int s_lo = lo;
+                // cached state of segment s_lo: end of it in the stream, entry
+                // index base, scale, tag
+                int64_t seg_end = (s_lo + 1 < nz) ? sh.start[s_lo + 1] : T;
+                int64_t qbase = sh.qb[s_lo];
+                V bvc = sh.bv[s_lo];
+                int64_t tagc = sh.tag[s_lo];
                 for (int64_t wb = p0; wb < p1; wb += 32) {
+                    const int64_t t = wb + lane;
+                    const bool valid = t < p1;
+                    if (wb + 32 <= seg_end) {
+                        // the whole window lies in segment s_lo
+                        emit(qbase + t, bvc, tagc, valid);
+                        if (wb + 32 == seg_end && s_lo + 1 < nz) {
+                            ++s_lo;
+                            seg_end = (s_lo + 1 < nz) ? sh.start[s_lo + 1] : T;
+                            qbase = sh.qb[s_lo]; bvc = sh.bv[s_lo]; tagc = sh.tag[s_lo];
+                        }
+                        continue;
+                    }
+                    // the window crosses segment starts: lane l's segment is
+                    // s_lo plus the number of starts at positions 1..l
                     const int j = s_lo + 1 + lane;
                     unsigned bit = 0u;
                     if (j < nz) {
-                        const int64_t sj = sh.start[j];
-                        if (sj < wb + 32) bit = 1u << (int)(sj - wb);
+                        const int64_t d = sh.start[j] - wb;
+                        if (d < 32) bit = 1u << (int)d;
                     }
                     const unsigned M = __reduce_or_sync(SPG_FULL, bit);
                     const int sg = s_lo + __popc(M & (0xffffffffu >> (31 - lane)));
-                    const int64_t t = wb + lane;
-                    const bool valid = t < p1;
                     const int sgv = valid ? sg : s_lo;
                     emit(sh.qb[sgv] + (valid ? t : sh.start[sgv]), sh.bv[sgv], sh.tag[sgv], valid);
                     s_lo += __popc(M);
                     if (s_lo + 1 < nz && sh.start[s_lo + 1] == wb + 32) ++s_lo;
+                    seg_end = (s_lo + 1 < nz) ? sh.start[s_lo + 1] : T;
+                    qbase = sh.qb[s_lo]; bvc = sh.bv[s_lo]; tagc = sh.tag[s_lo];
                 }
             }
         }
@@ -781,6 +801,7 @@ __global__ void __launch_bounds__(512, 2) k_num_dense(typename DSrc::Args sa, Ti
             atomic_add_v(&acc[r], src.val(q, bv));
             flg[r] = 1;
         };
+        (void)0;
         block_walk(src, emit, c.short_seg, c.huge_seg, sh);
         // compaction: each thread takes 4-row flag words; warp-aggregated slots
         const int64_t rbase = (int64_t)p << c.log2R;
@@ -809,6 +830,225 @@ __global__ void __launch_bounds__(512, 2) k_num_dense(typename DSrc::Args sa, Ti
                     }
                 }
             }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (sh.pos != mycnt) atomicOr(c.err, kErrCount);
+            sh.pos = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Heavy numeric by work items. For every heavy column the per-panel output
+// counts are cut, in panel order, into items: a panel holding at least
+// dense_min rows becomes a dense item (shared-memory accumulator over its
+// 2^log2R rows); runs of lighter panels are grouped into hash items of at most
+// kRangeCap output rows and kRangeMaxPanels panels (shared-memory hash table
+// keyed by the global row). Items of one column write consecutive, disjoint
+// ranges of the column's output, in panel order.
+// ---------------------------------------------------------------------------
+constexpr int kRangeCap = 4096;
+constexpr int kRangeMaxPanels = 16;
+constexpr int kRangeLog2T = 13;   // 8192 slots = 2 * kRangeCap
+
+struct HeavyItem {
+    int32_t g;      // global column
+    int32_t p0, p1; // panel range [p0, p1)
+    int32_t cnt;    // output rows of the item; negative: dense item
+    int32_t off;    // offset of the item's rows inside the column
+    int32_t pad;
+};
+
+// Cut heavy columns into work items (defined in util_kernels.cu).
+// mode 0: per-column item counts into ncount[h]; mode 1: write the items at
+// item_off[h] (exclusive scan of the counts).
+__global__ void k_heavy_items(const int32_t *list, const int32_t *list_off, const int64_t *sel,
+                              int hash_cap_max, int64_t c_lo, int64_t c_hi, const int32_t *pcnt,
+                              int P, int dense_min, int mode, int64_t *ncount,
+                              const int64_t *item_off, HeavyItem *items);
+
+// Range sources: the contributions of column g restricted to panels
+// [p0, p1). seg() yields segments; row(q, tag) is the global row.
+template <class I, class V> struct SrcPanelRange {
+    using Args = GemmArgs<I, V>;
+    using Val = V;
+    using Idx = I;
+    const ProbDev<I, V> *p;
+    const int64_t *ape;
+    const uint16_t *apr;
+    const V *apv;
+    int64_t b0, nb, k0, k1, ka;
+    int p0, np, log2R;
+    __device__ __forceinline__ void open(const Args &a, const TierCommon &c, int64_t g, int pp0,
+                                         int pp1, int) {
+        p = a.probs;
+        const int64_t bc = g - p->gcol0;
+        b0 = (int64_t)p->bp[bc];
+        nb = (int64_t)p->bp[bc + 1] - b0;
+        k0 = a.k0; k1 = a.k1; ka = p->ka;
+        p0 = pp0; np = pp1 - pp0; log2R = c.log2R;
+        ape = a.ap_end; apr = a.ap_row; apv = a.ap_val;
+    }
+    __device__ __forceinline__ int64_t nseg() const { return nb * np; }
+    __device__ __forceinline__ void seg(int64_t e2, int64_t &beg, int &len, V &bv, int64_t &tag) const {
+        const int64_t e = e2 / np;
+        const int pp = p0 + (int)(e2 - e * np);
+        const int64_t pe = b0 + e;
+        const int64_t k = (int64_t)p->bi[pe];
+        if (k < k0 || k >= k1) { len = 0; return; }
+        const int64_t idx = (int64_t)pp * ka + k;
+        const int64_t s = idx ? ape[idx - 1] : 0;
+        beg = s; len = (int)(ape[idx] - s); bv = p->bv[pe];
+        tag = (int64_t)pp << log2R;      // row base of the panel
+    }
+    __device__ __forceinline__ uint32_t row(int64_t q, int64_t tag) const {
+        return (uint32_t)(tag + apr[q]);
+    }
+    __device__ __forceinline__ V val(int64_t q, V bv) const { return mul_v(apv[q], bv); }
+};
+
+template <class I, class V> struct SrcPartsRange {
+    using Args = PartsArgs<I, V>;
+    using Val = V;
+    using Idx = I;
+    static constexpr int kShift = 40;
+    SrcParts<I, V> base;
+    int p0, p1, h, P;
+    int64_t r0, r1;
+    __device__ __forceinline__ void open(const Args &a, const TierCommon &c, int64_t g, int pp0,
+                                         int pp1, int hh) {
+        base.open(a, g);
+        p0 = pp0; p1 = pp1; h = hh; P = c.P;
+        r0 = (int64_t)pp0 << c.log2R;
+        r1 = (int64_t)pp1 << c.log2R;
+    }
+    __device__ __forceinline__ int64_t nseg() const { return base.nparts; }
+    __device__ __forceinline__ void seg(int64_t e, int64_t &beg, int &len, V &bv, int64_t &tag) const {
+        int64_t b, en;
+        base.range((int)e, b, en);
+        const int32_t *pc = base.parts[e].pcnt;
+        if (pc) {   // panel-grouped column: the range [p0, p1) is one run
+            const int32_t *rowc = pc + (int64_t)h * P;
+            int64_t off = 0, len2 = 0;
+            for (int q = 0; q < p0; ++q) off += rowc[q];
+            for (int q = p0; q < p1; ++q) len2 += rowc[q];
+            b += off;
+            en = b + len2;
+        }
+        beg = (e << kShift) | b; len = (int)(en - b); bv = V(1); tag = 0;
+    }
+    // rows outside the range (filter mode) map to kEmpty and are skipped
+    __device__ __forceinline__ uint32_t row(int64_t q, int64_t) const {
+        const int64_t r = (int64_t)base.row(q);
+        return (r >= r0 && r < r1) ? (uint32_t)r : kEmpty;
+    }
+    __device__ __forceinline__ V val(int64_t q, V) const { return base.val(q, V(1)); }
+};
+
+template <class DSrc>
+__global__ void __launch_bounds__(512, 2) k_num_heavy(typename DSrc::Args sa, TierCommon c,
+                                                      const HeavyItem *items, const int64_t *nitems_p,
+                                                      typename DSrc::Idx *out_rows,
+                                                      typename DSrc::Val *out_vals) {
+    using V = typename DSrc::Val;
+    using I = typename DSrc::Idx;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int R = 1 << c.log2R;
+    constexpr int T = 1 << kRangeLog2T;
+    // dense view: acc[R] values + flg[R] bytes; hash view: vals[T] + keys[T]
+    V *acc = reinterpret_cast<V *>(smem);
+    unsigned char *flg = smem + sizeof(V) * R;
+    uint32_t *flg4 = reinterpret_cast<uint32_t *>(flg);
+    V *hv = reinterpret_cast<V *>(smem);
+    uint32_t *hk = reinterpret_cast<uint32_t *>(smem + sizeof(V) * T);
+    __shared__ BlockShared<V> sh;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) { acc[r] = V(0); flg[r] = 0; }
+    if (threadIdx.x == 0) sh.pos = 0;
+    __syncthreads();
+    const int64_t nitems = *nitems_p;
+    const int lane = threadIdx.x & 31;
+    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const HeavyItem item = items[it];
+        const int64_t g = item.g;
+        if (g < c.c_lo || g >= c.c_hi) continue;
+        const bool dense = item.cnt < 0;
+        const int p0 = item.p0;
+        const int p1 = item.p1;
+        const int mycnt = dense ? -item.cnt : item.cnt;
+        const int64_t out0 = c.colptr[g] - c.out_base + item.off;
+        const int h = c.heavy_ord[g];
+        DSrc src;
+        src.open(sa, c, g, p0, p1, h);
+        if (dense) {
+            const int64_t rbase = (int64_t)p0 << c.log2R;
+            auto emit = [&](int64_t q, V bv, int64_t tag, bool valid) {
+                if (!valid) return;
+                const uint32_t gr = src.row(q, tag);
+                if (gr == kEmpty) return;
+                const int r = (int)((int64_t)gr - rbase);
+                atomic_add_v(&acc[r], src.val(q, bv));
+                flg[r] = 1;
+            };
+            block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+            for (int w0 = 0; w0 < (R >> 2); w0 += blockDim.x) {
+                const int w = w0 + threadIdx.x;
+                const uint32_t x = w < (R >> 2) ? flg4[w] : 0u;
+                const int n1 = __popc(x);
+                const int incl = warp_incl_scan(n1);
+                const int tot = __shfl_sync(SPG_FULL, incl, 31);
+                int wb = 0;
+                if (lane == 31 && tot) wb = atomicAdd(&sh.pos, tot);
+                wb = __shfl_sync(SPG_FULL, wb, 31);
+                if (x) {
+                    flg4[w] = 0u;
+                    int o = wb + incl - n1;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        if ((x >> (8 * b)) & 1u) {
+                            const int r = w * 4 + b;
+                            if (o < mycnt) {
+                                out_rows[out0 + o] = (I)(rbase + r);
+                                out_vals[out0 + o] = acc[r];
+                            }
+                            acc[r] = V(0);
+                            ++o;
+                        }
+                    }
+                }
+            }
+        } else {
+            for (int s = threadIdx.x; s < T; s += blockDim.x) { hk[s] = kEmpty; hv[s] = V(0); }
+            __syncthreads();
+            auto emit = [&](int64_t q, V bv, int64_t tag, bool valid) {
+                if (!valid) return;
+                const uint32_t gr = src.row(q, tag);
+                if (gr == kEmpty) return;
+                bool nw;
+                const int hh = hash_insert(hk, kRangeLog2T, gr, nw, c.err);
+                if (hh >= 0) atomic_add_v(&hv[hh], src.val(q, bv));
+            };
+            block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+            for (int s0 = 0; s0 < T; s0 += blockDim.x) {
+                const int s = s0 + threadIdx.x;
+                const uint32_t key = s < T ? hk[s] : kEmpty;
+                const bool occ = key != kEmpty;
+                const unsigned bal = __ballot_sync(SPG_FULL, occ);
+                int wbase = 0;
+                if (lane == 0 && bal) wbase = atomicAdd(&sh.pos, __popc(bal));
+                wbase = __shfl_sync(SPG_FULL, wbase, 0);
+                if (occ) {
+                    const int o = wbase + __popc(bal & ((1u << lane) - 1u));
+                    if (o < mycnt) {
+                        out_rows[out0 + o] = (I)key;
+                        out_vals[out0 + o] = hv[s];
+                    }
+                }
+            }
+            __syncthreads();
+            // the dense view shares this memory: restore its zero state
+            for (int r = threadIdx.x; r < R; r += blockDim.x) { acc[r] = V(0); flg[r] = 0; }
         }
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -138,6 +138,8 @@ struct PlanState {
     DevBuf ap_end, ap_row, ap_val;
     DevBuf stage_cnt, stage_colptr, stage_pcnt, drows, dvals, parts_tab;  // k-split
     DevBuf merge_tmp;
+    DevBuf items, item_cnt, item_off;    // heavy work items (dense panels / hash ranges)
+    int64_t n_items = 0;
     HostBuf h_colptr, h_small, h_stage_colptr, h_parts;
     std::vector<DevBuf> ring_col, ring_row, ring_val;   // spgemm_run_batched device ring
     std::vector<HostBuf> host_slots;                     // spgemm_run_batched pinned slots

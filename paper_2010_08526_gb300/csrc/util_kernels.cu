@@ -64,6 +64,50 @@ __global__ void k_bin_scatter(const uint8_t *tier, int64_t c_lo, int64_t c_hi,
     }
 }
 
+// mode 0: per-column item counts into ncount[h]; mode 1: write the items at
+// item_off[h] (exclusive scan of the counts). One thread per heavy column runs
+// the greedy cut over its P panel counts.
+__global__ void k_heavy_items(const int32_t *list, const int32_t *list_off, const int64_t *sel,
+                              int hash_cap_max, int64_t c_lo, int64_t c_hi, const int32_t *pcnt,
+                              int P, int dense_min, int mode, int64_t *ncount,
+                              const int64_t *item_off, HeavyItem *items) {
+    const int lo = list_off[kHeavyTier0], hi = list_off[kTiers];
+    const int nh = hi - lo;
+    const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= nh) return;
+    const int64_t g = list[lo + h];
+    int64_t n_items = 0;
+    if (g >= c_lo && g < c_hi && sel[g] > hash_cap_max) {
+        const int32_t *pc = pcnt + h * P;
+        int64_t w = mode ? item_off[h] : 0;
+        int gp0 = -1, gcnt = 0, off = 0, goff = 0;
+        auto flush = [&](int p_end) {
+            if (gp0 >= 0 && gcnt > 0) {
+                if (mode) items[w++] = HeavyItem{(int32_t)g, gp0, p_end, gcnt, goff, 0};
+                ++n_items;
+            }
+            gp0 = -1; gcnt = 0;
+        };
+        for (int p = 0; p < P; ++p) {
+            const int x = pc[p];
+            if (x >= dense_min) {
+                flush(p);
+                if (mode) items[w++] = HeavyItem{(int32_t)g, p, p + 1, -x, off, 0};
+                ++n_items;
+                off += x;
+                continue;
+            }
+            if (gp0 >= 0 && (gcnt + x > kRangeCap || p - gp0 >= kRangeMaxPanels)) flush(p);
+            if (x == 0 && gp0 < 0) continue;      // no open group: skip empty panels
+            if (gp0 < 0) { gp0 = p; goff = off; }
+            gcnt += x;
+            off += x;
+        }
+        flush(P);
+    }
+    if (!mode) ncount[h] = n_items;
+}
+
 // ---- exclusive scan of int64 (three phases, all on the device) ------------
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;
