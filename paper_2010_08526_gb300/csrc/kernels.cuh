@@ -614,14 +614,26 @@ __global__ void __launch_bounds__(1024, 1) k_sym_bitmap(typename Src::Args sa, T
         const int64_t rows = (mrows - r0) < c.Rs ? (mrows - r0) : c.Rs;
         const int nwords = (int)((rows + 31) >> 5);
         const bool filt = c.Q > 1;
+        // Lanes of a window often mark the same bitmap word (rows of one A
+        // column are clustered): a shuffle-based OR over lanes with equal
+        // words leaves one shared atomic per run of equal words.
         auto emit = [&](int64_t qq, V, int64_t, bool valid) {
-            if (!valid) return;
-            int64_t r = (int64_t)src.row(qq);
-            if (filt) {
+            const int lane = threadIdx.x & 31;
+            int64_t r = valid ? (int64_t)src.row(qq) : -1;
+            if (filt && r >= 0) {
                 r -= r0;
-                if (r < 0 || r >= rows) return;
+                if (r >= rows) r = -1;
             }
-            atomicOr(&bm[r >> 5], 1u << (r & 31));
+            const unsigned w = r >= 0 ? (unsigned)(r >> 5) : 0x80000000u + lane;
+            unsigned b = r >= 0 ? 1u << (r & 31) : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned w2 = __shfl_down_sync(SPG_FULL, w, o);
+                const unsigned b2 = __shfl_down_sync(SPG_FULL, b, o);
+                if (lane + o < 32 && w2 == w) b |= b2;
+            }
+            const unsigned wprev = __shfl_up_sync(SPG_FULL, w, 1);
+            if (r >= 0 && (lane == 0 || wprev != w)) atomicOr(&bm[w], b);
         };
         block_walk(src, emit, c.short_seg, c.huge_seg, sh);
         const int h = c.heavy_ord[g];

@@ -212,6 +212,23 @@ def test_ksplit_merge_equals_unsplit(s):
     assert info["flops"] >= info["unmerged_nnz"] >= info["nnz_c"]   # Eq. (1)
 
 
+def test_repeated_symbolic_keeps_the_batch_plan():
+    A = skewed(3000, 3000, 63, hubs=3, hub_deg=1200)
+    Ad = to_dev(A)
+    ref = oracle.spgemm(A, A)
+    for kst in (1, 3):
+        plan = spg.Plan(Ad, Ad, kstages=kst, budget=A.bytes() * 2 + (1 << 20) + ref.nnz * 12)
+        first = [plan.batch(t) for t in range(plan.symbolic()["nbatches"])]
+        outs = [plan.alloc_batch(t) for t in range(len(first))]
+        for _ in range(2):
+            info = plan.symbolic()
+            assert [plan.batch(t) for t in range(info["nbatches"])] == first
+            for t in range(len(first)):
+                plan.numeric(t, out=outs[t])
+        plan.check_errors()
+        plan.close()
+
+
 @pytest.mark.parametrize("vt", [np.float32, np.int64])
 def test_ksplit_heavy_dense_merge(vt):
     dist = "normal" if vt != np.int64 else "ones"
