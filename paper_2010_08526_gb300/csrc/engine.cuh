@@ -538,7 +538,11 @@ template <class I, class V> struct Engine : EngineBase {
         const int64_t ptr_bytes = 8;
         const int64_t inputs = (int64_t)(ps.A.nnz + ps.B.nnz) * r +
                                (ps.A.ncols + 1 + ps.B.ncols + 1) * (ps.idx64 ? 8 : 4);
-        const int64_t ws = (int64_t)ps.workspace_bytes();
+        // the stage partial buffers are part of each batch's bytes (w_j counts
+        // the unmerged entries), so they are not workspace here; this keeps the
+        // plan identical across repeated symbolic calls on one plan
+        const int64_t ws = (int64_t)ps.workspace_bytes() - (int64_t)ps.drows.bytes -
+                           (int64_t)ps.dvals.bytes - (int64_t)ps.parts_tab.bytes;
         const int64_t avail = (int64_t)ps.budget - inputs - ws;
         const int ring = ps.opts.ring_depth > 0 ? ps.opts.ring_depth : 2;
         if (avail <= 0) {
