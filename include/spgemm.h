@@ -249,6 +249,26 @@ spgemm_status spgemm_merge(const spgemm_csc *parts, int nparts, spgemm_csc *out,
                            cudaStream_t stream);
 
 /*
+ * spgemm_merge_noalloc -- the same merge as spgemm_merge (same arguments, same
+ * two-call protocol, unsorted output) for callers that may not allocate device
+ * memory, e.g. code running under another framework's fixed device-memory pool
+ * or in a loop where cudaMalloc's implicit synchronisation is not acceptable.
+ * The paper has no counterpart; this is a calling convention of the library.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its work
+ * buffers live in one 32 MiB device array that every GPU loading the library
+ * keeps until exit, so it accepts at most about 1.1 million columns
+ * (29 bytes per column plus a few KiB) and at most 64 parts, and every merged
+ * column must hold at most 8192 distinct rows (the shared-memory hash tables);
+ * larger inputs return SPGEMM_ERR_INVALID with the limit in the message. The
+ * first call on each device looks up the array's address on that device, so
+ * make it before any stream capture. All calls share the array (it keeps the
+ * last call's contents): calls that overlap on the GPU race, so serialise them.
+ * Errors: as spgemm_merge, plus SPGEMM_ERR_INVALID for sizes beyond the array.
+ */
+spgemm_status spgemm_merge_noalloc(const spgemm_csc *parts, int nparts, spgemm_csc *out,
+                                   cudaStream_t stream);
+
+/*
  * Sink for spgemm_run_batched. Called on the calling host thread once per
  * finished piece of C: columns [col_begin, col_end) of C, a CSC whose arrays
  * are PINNED HOST memory owned by the library and valid only during the call

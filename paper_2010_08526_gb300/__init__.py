@@ -25,6 +25,7 @@ from .core import (
     Tuning,
     spgemm,
     merge,
+    merge_noalloc,
     run_batched,
     backward,
     SpGEMMFn,
@@ -32,6 +33,6 @@ from .core import (
 )
 
 __all__ = [
-    "SpgemmError", "load", "Csc", "Plan", "Tuning", "spgemm", "merge", "run_batched",
+    "SpgemmError", "load", "Csc", "Plan", "Tuning", "spgemm", "merge", "merge_noalloc", "run_batched",
     "backward", "SpGEMMFn", "Multi",
 ]

@@ -85,6 +85,7 @@ SIGNATURES = {
     "spgemm_plan_stats": (ctypes.c_int, [vp, ctypes.c_int, P(SpgemmStats)]),
     "spgemm_numeric": (ctypes.c_int, [vp, i64, P(SpgemmCsc), vp]),
     "spgemm_merge": (ctypes.c_int, [P(SpgemmCsc), ctypes.c_int, P(SpgemmCsc), vp]),
+    "spgemm_merge_noalloc": (ctypes.c_int, [P(SpgemmCsc), ctypes.c_int, P(SpgemmCsc), vp]),
     "spgemm_run_batched": (ctypes.c_int, [vp, SINK_FN, vp, vp, vp]),
     "spgemm_backward": (ctypes.c_int, [vp, P(SpgemmCsc), vp, vp, vp]),
     "spgemm_multi_create": (ctypes.c_int, [ctypes.c_int, P(SpgemmCsc), P(SpgemmCsc),

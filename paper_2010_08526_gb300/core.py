@@ -258,9 +258,10 @@ def spgemm(A: Csc, B: Csc, *, budget: Optional[int] = None, kstages: int = 1,
         plan.close()
 
 
-def merge(parts: List[Csc], ptr_dtype=torch.int64, stream=None) -> Csc:
+def merge(parts: List[Csc], ptr_dtype=torch.int64, stream=None, _entry="spgemm_merge") -> Csc:
     """Sort-free hash merge: out(:, j) = sum_i parts[i](:, j)."""
     lib = load()
+    fn = getattr(lib, _entry)
     if not parts:
         raise ValueError("no parts")
     p0 = parts[0]
@@ -272,15 +273,21 @@ def merge(parts: List[Csc], ptr_dtype=torch.int64, stream=None) -> Csc:
     so.vals = 0
     so.nnz = 0
     st = _stream_handle(stream)
-    check(lib.spgemm_merge(arr, len(parts), ctypes.byref(so), st))
+    check(fn(arr, len(parts), ctypes.byref(so), st))
     nnz = int(so.nnz)
     out.rowidx = torch.empty(nnz, dtype=p0.rowidx.dtype, device=p0.device)
     out.vals = torch.empty(nnz, dtype=p0.vals.dtype, device=p0.device)
     so2 = out.struct()
     if nnz == 0:
         return out
-    check(lib.spgemm_merge(arr, len(parts), ctypes.byref(so2), st))
+    check(fn(arr, len(parts), ctypes.byref(so2), st))
     return out
+
+
+def merge_noalloc(parts: List[Csc], ptr_dtype=torch.int64, stream=None) -> Csc:
+    """The same merge through spgemm_merge_noalloc, which allocates no device
+    memory of its own (the output buffers are still allocated here, by torch)."""
+    return merge(parts, ptr_dtype, stream, _entry="spgemm_merge_noalloc")
 
 
 def run_batched(plan: Plan, sink: Callable[[int, int, int, tuple], Optional[int]],

@@ -375,6 +375,14 @@ spgemm_status spgemm_plan_check(const spgemm_plan *plan, cudaStream_t stream) {
 }
 
 spgemm_status spgemm_merge(const spgemm_csc *parts, int nparts, spgemm_csc *out, cudaStream_t stream) {
+    spgemm_status s = check_merge_args(parts, nparts, out);
+    if (s != SPGEMM_OK) return s;
+    return merge_dispatch(parts, nparts, out, stream);
+}
+
+}  // extern "C"
+
+spgemm_status spg::check_merge_args(const spgemm_csc *parts, int nparts, const spgemm_csc *out) {
     if (!parts || nparts < 1 || !out) { set_error("bad arguments"); return SPGEMM_ERR_INVALID; }
     spgemm_status s;
     for (int i = 0; i < nparts; ++i) {
@@ -391,8 +399,10 @@ spgemm_status spgemm_merge(const spgemm_csc *parts, int nparts, spgemm_csc *out,
     }
     if (out->rowidx && out->nnz > 0 && !out->vals) { set_error("out->vals is NULL"); return SPGEMM_ERR_INVALID; }
     if (parts[0].ncols >= 0x7fffffffLL) { set_error("ncols must be < 2^31-1"); return SPGEMM_ERR_INVALID; }
-    return merge_dispatch(parts, nparts, out, stream);
+    return SPGEMM_OK;
 }
+
+extern "C" {
 
 spgemm_status spgemm_multi_create(int nprob, const spgemm_csc *As, const spgemm_csc *Bs,
                                   const spgemm_opts *opts, cudaStream_t stream, spgemm_multi **out) {

@@ -253,7 +253,7 @@ template <class I, class V> struct Engine : EngineBase {
                            const int64_t *bound, int64_t *f_out, uint8_t *tier, int64_t *cnt_out,
                            int32_t *list, int32_t *off, int32_t *heavy_ord_w,
                            const int32_t *heavy_ord_r, DevBuf *pcnt_grow, int32_t *pcnt_ptr,
-                           int *hist_out, cudaStream_t st) {
+                           int *hist_out, cudaStream_t st, bool allow_heavy = true) {
         const int64_t nc = c_hi - c_lo;
         SPG_CK(cudaMemsetAsync(cx.hist, 0, sizeof(int32_t) * 64, st));
         SPG_CK(cudaMemsetAsync(cx.cursor, 0, sizeof(int32_t) * 64, st));
@@ -276,6 +276,11 @@ template <class I, class V> struct Engine : EngineBase {
         if (hist_out) std::memcpy(hist_out, hist, sizeof(hist));
         int nheavy = 0;
         for (int t = kHeavyTier0; t < kTiers; ++t) nheavy += hist[t];
+        if (nheavy && !allow_heavy) {
+            set_error("a column may hold more than " + std::to_string(cx.tun.hash_cap_max) +
+                      " distinct rows, above the shared-memory hash tables this call may use");
+            return SPGEMM_ERR_INVALID;
+        }
         TierCommon c = common_of(cx);
         c.list = list; c.list_off = off; c.cnt = cnt_out;
         const int th = cx.tbegin(kPhSymHash, st);
@@ -853,6 +858,102 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(cudaStreamSynchronize(st));
         if (errw) {
             set_error("merge: device error flags " + std::to_string(errw));
+            return SPGEMM_ERR_OVERFLOW;
+        }
+        return SPGEMM_OK;
+    }
+
+    // ---- merge into caller-free scratch (spgemm_merge_noalloc) ----------------
+    // Same two-call protocol and kernels as merge(), with every work buffer
+    // carved from the given device scratch and host staging in static memory;
+    // no allocation of any kind. Columns must fit the shared-memory hash tiers.
+    static size_t merge_noalloc_bytes(int64_t n, int nparts) {
+        auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+        return al(sizeof(int64_t) * (n + 1)) * 2 + al(n + 16) + al(sizeof(int32_t) * (n + 1)) * 3 +
+               al(sizeof(int32_t) * 64) * 4 + al(sizeof(int) * 4) +
+               al(sizeof(int64_t) * scan_partials_len(n + 1)) + al(sizeof(PartDev<I, V>) * nparts);
+    }
+
+    static spgemm_status merge_noalloc(const spgemm_csc *parts, int nparts, spgemm_csc *out,
+                                       cudaStream_t st, unsigned char *scratch, size_t cap,
+                                       int32_t *h_stage, int nsm) {
+        const int64_t n = parts[0].ncols, m = parts[0].nrows;
+        const size_t need = merge_noalloc_bytes(n, nparts);
+        attrs();
+        if (need > cap) {
+            set_error("merge_noalloc: " + std::to_string(n) + " columns and " + std::to_string(nparts) +
+                      " parts need " + std::to_string(need) + " B of scratch; the static scratch holds " +
+                      std::to_string(cap) + " B");
+            return SPGEMM_ERR_INVALID;
+        }
+        auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+        unsigned char *p = scratch;
+        auto take = [&](size_t bytes) { unsigned char *q = p; p += al(bytes); return q; };
+        int64_t *cnt = (int64_t *)take(sizeof(int64_t) * (n + 1));
+        int64_t *colptr = (int64_t *)take(sizeof(int64_t) * (n + 1));
+        uint8_t *tier = (uint8_t *)take(n + 16);
+        int32_t *list_sym = (int32_t *)take(sizeof(int32_t) * (n + 1));
+        int32_t *list_num = (int32_t *)take(sizeof(int32_t) * (n + 1));
+        int32_t *heavy_ord = (int32_t *)take(sizeof(int32_t) * (n + 1));
+        int32_t *hist = (int32_t *)take(sizeof(int32_t) * 64);
+        int32_t *cursor = (int32_t *)take(sizeof(int32_t) * 64);
+        int32_t *off_sym = (int32_t *)take(sizeof(int32_t) * 64);
+        int32_t *off_num = (int32_t *)take(sizeof(int32_t) * 64);
+        int *err = (int *)take(sizeof(int) * 4);
+        int64_t *part_sc = (int64_t *)take(sizeof(int64_t) * scan_partials_len(n + 1));
+        PartDev<I, V> *tab_d = (PartDev<I, V> *)take(sizeof(PartDev<I, V>) * nparts);
+        PartDev<I, V> tab[64];
+        for (int i = 0; i < nparts; ++i) {
+            tab[i].colptr = parts[i].colptr;
+            tab[i].ptr64 = parts[i].ptr_type == SPGEMM_I64;
+            tab[i].sub = 0;
+            tab[i].rows = (const I *)parts[i].rowidx;
+            tab[i].vals = (const V *)parts[i].vals;
+            tab[i].pcnt = nullptr;
+        }
+        // the scratch keeps the previous call's contents: clear what is read
+        // before it is written (error word; tier histogram and cursors are
+        // cleared inside the passes)
+        SPG_CK(cudaMemcpyAsync(tab_d, tab, sizeof(PartDev<I, V>) * nparts, cudaMemcpyHostToDevice, st));
+        SPG_CK(cudaMemsetAsync(err, 0, sizeof(int) * 4, st));
+        Ctx cx;
+        cx.nsm = nsm;
+        cx.err = err; cx.hist = hist; cx.cursor = cursor; cx.h_small = h_stage;
+        cx.tun.log2R = sizeof(V) == 4 ? 14 : 13;
+        cx.P = 1; cx.Q = 1; cx.Rs = 32;
+        PA pa{tab_d, nparts, m};
+        int hist_h[16];
+        // columns above the largest hash table would need the dense path's
+        // per-panel workspace: sym_pass rejects them before any launch
+        SPG_ST(sym_pass<SrcParts<I, V>>(cx, pa, 0, n, nullptr, nullptr, tier, cnt, list_sym, off_sym,
+                                        heavy_ord, heavy_ord, nullptr, nullptr, hist_h, st, false));
+        SPG_CK(exclusive_scan_i64(cnt, n, colptr, part_sc, 1, st));
+        int64_t nnz = 0;
+        SPG_CK(cudaMemcpyAsync(&nnz, colptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        if (out->ptr_type == SPGEMM_I32 && nnz > 0x7fffffffLL) {
+            set_error("merged nnz does not fit a 32-bit colptr");
+            return SPGEMM_ERR_INDEX_OVERFLOW;
+        }
+        if (!out->rowidx) {
+            SPG_CK(rebase_colptr(colptr, n, out->colptr, out->ptr_type == SPGEMM_I64, st));
+            out->nnz = nnz;
+            SPG_CK(cudaStreamSynchronize(st));
+            return SPGEMM_OK;
+        }
+        if (out->nnz != nnz) {
+            set_error("out->nnz does not match the merged size");
+            return SPGEMM_ERR_INVALID;
+        }
+        NumOut<I, V> o{colptr, 0, (I *)out->rowidx, (V *)out->vals};
+        SPG_ST((num_pass<SrcParts<I, V>, SrcPartsPanel<I, V>>(
+            cx, pa, pa, 0, n, cnt, cnt, o, nullptr, false, list_sym, off_sym, heavy_ord, nullptr, tier,
+            list_num, off_num, st)));
+        int errw = 0;
+        SPG_CK(cudaMemcpyAsync(&errw, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        if (errw) {
+            set_error("merge_noalloc: device error flags " + std::to_string(errw));
             return SPGEMM_ERR_OVERFLOW;
         }
         return SPGEMM_OK;

@@ -8,6 +8,11 @@ namespace spg {
     spgemm_status merge_##I##_##V(const spgemm_csc *, int, spgemm_csc *, cudaStream_t);     \
     spgemm_status multi_create_##I##_##V(MultiState &, const spgemm_csc *, const spgemm_csc *, \
                                          cudaStream_t);
+#define SPG_DECL2(I, V)                                                                     \
+    spgemm_status merge_noalloc_##I##_##V(const spgemm_csc *, int, spgemm_csc *, cudaStream_t,   \
+                                          unsigned char *, size_t, int32_t *, int);
+SPG_DECL2(i32, f64) SPG_DECL2(i32, f32) SPG_DECL2(i32, i64v)
+SPG_DECL2(i64, f64) SPG_DECL2(i64, f32) SPG_DECL2(i64, i64v)
 SPG_DECL(i32, f64) SPG_DECL(i32, f32) SPG_DECL(i32, i64v)
 SPG_DECL(i64, f64) SPG_DECL(i64, f32) SPG_DECL(i64, i64v)
 
@@ -35,6 +40,18 @@ spgemm_status merge_dispatch(const spgemm_csc *parts, int nparts, spgemm_csc *ou
 #define MG(I, V) merge_##I##_##V(parts, nparts, out, st)
     SPG_SWITCH(idx64, vtype, MG)
 #undef MG
+    set_error("unsupported type combination");
+    return SPGEMM_ERR_INVALID;
+}
+
+spgemm_status merge_noalloc_dispatch(const spgemm_csc *parts, int nparts, spgemm_csc *out,
+                                     cudaStream_t st, unsigned char *scratch, size_t cap,
+                                     int32_t *stage, int nsm) {
+    const int idx64 = parts[0].idx_type == SPGEMM_I64;
+    const int vtype = parts[0].val_type;
+#define MN(I, V) merge_noalloc_##I##_##V(parts, nparts, out, st, scratch, cap, stage, nsm)
+    SPG_SWITCH(idx64, vtype, MN)
+#undef MN
     set_error("unsupported type combination");
     return SPGEMM_ERR_INVALID;
 }

@@ -10,4 +10,8 @@ spgemm_status multi_create_i32_f32(MultiState &ms, const spgemm_csc *A, const sp
                                      cudaStream_t st) {
     return Engine<int32_t, float>::multi_create(ms, A, B, st);
 }
+spgemm_status merge_noalloc_i32_f32(const spgemm_csc *p, int np, spgemm_csc *o, cudaStream_t st,
+                                     unsigned char *scratch, size_t cap, int32_t *stage, int nsm) {
+    return Engine<int32_t, float>::merge_noalloc(p, np, o, st, scratch, cap, stage, nsm);
+}
 }  // namespace spg

@@ -10,4 +10,8 @@ spgemm_status multi_create_i64_i64v(MultiState &ms, const spgemm_csc *A, const s
                                      cudaStream_t st) {
     return Engine<int64_t, int64_t>::multi_create(ms, A, B, st);
 }
+spgemm_status merge_noalloc_i64_i64v(const spgemm_csc *p, int np, spgemm_csc *o, cudaStream_t st,
+                                     unsigned char *scratch, size_t cap, int32_t *stage, int nsm) {
+    return Engine<int64_t, int64_t>::merge_noalloc(p, np, o, st, scratch, cap, stage, nsm);
+}
 }  // namespace spg

@@ -176,6 +176,14 @@ struct EngineBase {
 spgemm_status merge_dispatch(const spgemm_csc *parts, int nparts, spgemm_csc *out,
                              cudaStream_t st);
 
+// The merge with caller-free scratch (spgemm_merge_noalloc).
+spgemm_status merge_noalloc_dispatch(const spgemm_csc *parts, int nparts, spgemm_csc *out,
+                                     cudaStream_t st, unsigned char *scratch, size_t cap,
+                                     int32_t *stage, int nsm);
+
+// Argument checks shared by the merge entry points.
+spgemm_status check_merge_args(const spgemm_csc *parts, int nparts, const spgemm_csc *out);
+
 EngineBase *make_engine(int idx64, int vtype);
 
 // thread-local error message
