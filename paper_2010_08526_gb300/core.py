@@ -230,9 +230,11 @@ class Plan:
 
 
 def spgemm(A: Csc, B: Csc, *, budget: Optional[int] = None, kstages: int = 1,
-           tuning: Optional[Tuning] = None, validate: bool = False, stream=None) -> Csc:
+           tuning: Optional[Tuning] = None, validate: bool = False, stream=None,
+           ptr_dtype=torch.int64) -> Csc:
     """C = A*B as one device CSC (batches computed one after another into
-    slices of the full output). Rows inside columns are unsorted."""
+    slices of the full output). Rows inside columns are unsorted. ptr_dtype
+    torch.int32 gives a colptr of the input index type (if nnz(C) fits)."""
     plan = Plan(A, B, budget=budget, kstages=kstages, tuning=tuning, validate=validate,
                 stream=stream)
     try:
@@ -241,7 +243,7 @@ def spgemm(A: Csc, B: Csc, *, budget: Optional[int] = None, kstages: int = 1,
         dev = A.device
         rows = torch.empty(nnz, dtype=A.rowidx.dtype, device=dev)
         vals = torch.empty(nnz, dtype=A.vals.dtype, device=dev)
-        colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=dev)
+        colptr = torch.empty(B.ncols + 1, dtype=ptr_dtype, device=dev)
         scratch = torch.empty(int(info["max_batch_cols"]) + 1, dtype=torch.int64, device=dev)
         off = 0
         for t in range(plan.nbatches):
@@ -249,8 +251,8 @@ def spgemm(A: Csc, B: Csc, *, budget: Optional[int] = None, kstages: int = 1,
             plan.numeric_into(t, scratch[: c1 - c0 + 1], rows[off:off + bn], vals[off:off + bn],
                               stream)
             off += bn
-        check(plan._lib.spgemm_plan_colptr(plan._h, ctypes.c_void_p(colptr.data_ptr()), C.I64,
-                                           _stream_handle(stream)))
+        check(plan._lib.spgemm_plan_colptr(plan._h, ctypes.c_void_p(colptr.data_ptr()),
+                                           _IDX[ptr_dtype], _stream_handle(stream)))
         out = Csc(A.nrows, B.ncols, colptr, rows, vals)
         out.plan_info = info
         return out

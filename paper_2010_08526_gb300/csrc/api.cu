@@ -24,7 +24,7 @@ size_t PlanState::workspace_bytes() const {
                             &off_sym, &off_num, &heavy_ord, &pcnt, &err, &scan_part, &wbytes,
                             &valid_flag, &ap_end, &ap_row, &ap_val, &stage_cnt, &stage_colptr,
                             &stage_pcnt, &merge_tmp, &drows, &dvals, &parts_tab, &items, &item_cnt,
-                            &item_off};
+                            &item_off, &item_order};
     size_t s = 0;
     for (auto *b : bufs) s += b->bytes;
     return s;
@@ -35,7 +35,7 @@ void PlanState::release_all() {
                       &off_sym, &off_num, &heavy_ord, &pcnt, &err, &scan_part, &wbytes,
                       &valid_flag, &ap_end, &ap_row, &ap_val, &stage_cnt, &stage_colptr,
                       &stage_pcnt, &merge_tmp, &drows, &dvals, &parts_tab, &items, &item_cnt,
-                      &item_off};
+                      &item_off, &item_order};
     for (auto *b : bufs) b->release();
     h_colptr.release();
     h_small.release();

@@ -46,6 +46,7 @@ struct Ctx {
     int64_t Rs;
     PhaseTimer *tm = nullptr;   // optional phase timing and launch counting
     int ph_hash = kPhNumHash, ph_dense = kPhNumDense;
+    bool stage_items = false;   // heavy items take their counts from pcnt_in
     int tbegin(int phase, cudaStream_t st) const { return tm ? tm->begin(phase, st) : -1; }
     void tend(int idx, cudaStream_t st) const { if (tm) tm->end(idx, st); }
     void launched(int n = 1) const { if (tm) tm->launches += n; }
@@ -216,8 +217,8 @@ template <class I, class V> struct Engine : EngineBase {
     static spgemm_status build_items(const Ctx &cx, int nheavy, const int32_t *sym_list,
                                      const int32_t *sym_off, const int64_t *sel,
                                      const int32_t *pcnt, int64_t n, DevBuf &items, DevBuf &icnt,
-                                     DevBuf &ioff, DevBuf &scan_part, int64_t *n_items,
-                                     cudaStream_t st) {
+                                     DevBuf &ioff, DevBuf &scan_part, DevBuf &order,
+                                     int64_t *n_items, cudaStream_t st) {
         *n_items = 0;
         if (!nheavy) return SPGEMM_OK;
         SPG_CK(icnt.ensure(sizeof(int64_t) * (nheavy + 1)));
@@ -238,7 +239,18 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(items.ensure(sizeof(HeavyItem) * (size_t)(total + 1)));
         k_heavy_items<<<nb, 256, 0, st>>>(sym_list, sym_off, sel, cx.tun.hash_cap_max, 0, n, pcnt, cx.P,
                                           dmin, 1, nullptr, ioff.as<int64_t>(), items.as<HeavyItem>());
-        cx.launched(5);
+        // panel-major processing order: item indices sorted by first panel,
+        // stored after the items (icnt is reused for the panel histogram)
+        SPG_CK(order.ensure(sizeof(int32_t) * (size_t)(total + 1)));
+        SPG_CK(icnt.ensure(sizeof(int64_t) * (size_t)(std::max(nheavy, cx.P) + 1)));
+        int32_t *pc = reinterpret_cast<int32_t *>(icnt.p);
+        SPG_CK(cudaMemsetAsync(pc, 0, sizeof(int32_t) * (cx.P + 1), st));
+        const int64_t *tot_d = ioff.as<int64_t>() + nheavy;
+        const unsigned ob = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096));
+        k_items_by_panel<<<ob, 256, 0, st>>>(items.as<HeavyItem>(), tot_d, 0, pc, nullptr);
+        k_small_excl_scan<<<1, 1024, 0, st>>>(pc, cx.P);
+        k_items_by_panel<<<ob, 256, 0, st>>>(items.as<HeavyItem>(), tot_d, 1, pc, order.as<int32_t>());
+        cx.launched(8);
         SPG_CK(cudaGetLastError());
         *n_items = total;
         return SPGEMM_OK;
@@ -317,7 +329,8 @@ template <class I, class V> struct Engine : EngineBase {
                            const int32_t *sym_off, const int32_t *heavy_ord,
                            const int32_t *pcnt_in, uint8_t *tier, int32_t *list, int32_t *off,
                            cudaStream_t st, const HeavyItem *items = nullptr,
-                           const int64_t *n_items_dev = nullptr, int64_t n_items = 0) {
+                           const int64_t *n_items_dev = nullptr, int64_t n_items = 0,
+                           const int32_t *item_order = nullptr) {
         const int64_t nc = c_hi - c_lo;
         bool any_hash = tc == nullptr;
         if (tc) for (int t = 1; t <= 8; ++t) any_hash |= tc[t] > 0;
@@ -348,13 +361,15 @@ template <class I, class V> struct Engine : EngineBase {
             c.heavy_ord = heavy_ord;
             c.pcnt_in = pcnt_in;
             c.c_lo = c_lo; c.c_hi = c_hi;
+            c.item_counts_from_pcnt = cx.stage_items ? 1 : 0;
             if constexpr (!std::is_same<RSrc, DSrc>::value) {
               if (items) {
                 const int smem = heavy_smem(cx);
                 const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 34 * 1024)));
                 const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * per_sm));
                 const int td = cx.tbegin(cx.ph_dense, st);
-                k_num_heavy<RSrc><<<blocks, 512, smem, st>>>(da, c, items, n_items_dev, o.rows, o.vals);
+                k_num_heavy<RSrc><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items_dev,
+                                                             o.rows, o.vals);
                 cx.tend(td, st);
                 cx.launched();
                 SPG_CK(cudaGetLastError());
@@ -474,7 +489,7 @@ template <class I, class V> struct Engine : EngineBase {
         if (ps.nheavy) SPG_ST(build_panels(ps, st));
         SPG_ST(build_items(cx, ps.nheavy, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                            ps.cnt.as<int64_t>(), ps.pcnt.as<int32_t>(), n, ps.items, ps.item_cnt,
-                           ps.item_off, ps.scan_part, &ps.n_items, st));
+                           ps.item_off, ps.scan_part, ps.item_order, &ps.n_items, st));
         SPG_CK(cudaStreamSynchronize(st));
         const int errw = *(int *)(ps.h_small.as<char>() + 256);
         if (errw) {
@@ -659,7 +674,7 @@ template <class I, class V> struct Engine : EngineBase {
                 b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                 ps.heavy_ord.as<int32_t>(), ps.pcnt.as<int32_t>(), ps.tier.as<uint8_t>(),
                 ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
-                ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items)));
+                ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
         } else {
             const int64_t *hs = ps.h_stage_colptr.as<int64_t>();
             for (int s = 0; s < ps.s; ++s) {
@@ -671,11 +686,16 @@ template <class I, class V> struct Engine : EngineBase {
                 GA ga = gemm_args(ps, k0, k1);
                 const int32_t *spc = ps.nheavy ? ps.stage_pcnt.as<int32_t>() + (size_t)s * ps.nheavy * ps.P
                                                : nullptr;
-                SPG_ST((num_pass<SrcGemm<I, V>, SrcPanel<I, V>>(
+                // heavy columns: the merge's work items with this stage's counts,
+                // so each stage column is grouped by the ranges the merge reads
+                cx.stage_items = true;
+                SPG_ST((num_pass<SrcGemm<I, V>, SrcPanel<I, V>, SrcPanelRange<I, V>>(
                     cx, ga, ga, b.c0, b.c1, scnt, ps.cnt.as<int64_t>(), o, b.tc[1 + s].data(),
                     b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                     ps.heavy_ord.as<int32_t>(), spc, ps.tier.as<uint8_t>(), ps.list_num.as<int32_t>(),
-                    ps.off_num.as<int32_t>(), st)));
+                    ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
+                    ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
+                cx.stage_items = false;
             }
             // sort-free hash merge of the stage partials (Sec. IV-D)
             cx.ph_hash = kPhMerge;
@@ -687,7 +707,7 @@ template <class I, class V> struct Engine : EngineBase {
                 b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                 ps.heavy_ord.as<int32_t>(), ps.pcnt.as<int32_t>(), ps.tier.as<uint8_t>(),
                 ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
-                ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items)));
+                ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
         }
         SPG_CK(rebase_colptr(ps.colptr.as<int64_t>() + b.c0, b.c1 - b.c0, C->colptr,
                              C->ptr_type == SPGEMM_I64, st));
@@ -845,14 +865,14 @@ template <class I, class V> struct Engine : EngineBase {
         int64_t n_items = 0;
         SPG_ST(build_items(cx, nheavy, tmp.list_sym.as<int32_t>(), tmp.off_sym.as<int32_t>(),
                            tmp.cnt.as<int64_t>(), tmp.pcnt.as<int32_t>(), n, tmp.items, tmp.item_cnt,
-                           tmp.item_off, tmp.scan_part, &n_items, st));
+                           tmp.item_off, tmp.scan_part, tmp.item_order, &n_items, st));
         NumOut<I, V> o{tmp.colptr.as<int64_t>(), 0, (I *)out->rowidx, (V *)out->vals};
         SPG_ST((num_pass<SrcParts<I, V>, SrcPartsPanel<I, V>, SrcPartsRange<I, V>>(
             cx, pa, pa, 0, n, tmp.cnt.as<int64_t>(), tmp.cnt.as<int64_t>(), o, nullptr, nheavy > 0,
             tmp.list_sym.as<int32_t>(), tmp.off_sym.as<int32_t>(), tmp.heavy_ord.as<int32_t>(),
             tmp.pcnt.as<int32_t>(), tmp.tier.as<uint8_t>(), tmp.list_num.as<int32_t>(),
             tmp.off_num.as<int32_t>(), st, tmp.items.as<HeavyItem>(),
-            tmp.item_off.as<int64_t>() + nheavy, n_items)));
+            tmp.item_off.as<int64_t>() + nheavy, n_items, tmp.item_order.as<int32_t>())));
         int errw = 0;
         SPG_CK(cudaMemcpyAsync(&errw, tmp.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         SPG_CK(cudaStreamSynchronize(st));

@@ -82,6 +82,7 @@ struct TierCommon {
     int64_t Rs;              // symbolic bitmap rows per item
     int Q;                   // symbolic panels per column
     int64_t c_lo, c_hi;      // global column range (dense items)
+    int item_counts_from_pcnt; // heavy items: take count / offset from pcnt_in (a k-stage)
 };
 
 template <class I, class V> struct GemmArgs {
@@ -119,13 +120,13 @@ template <class I, class V> struct SrcGemm {
     __device__ __forceinline__ int64_t m() const { return p->m; }
     __device__ __forceinline__ void seg(int64_t e, int64_t &beg, int &len, V &bv, int64_t &tag) const {
         const int64_t pe = b0 + e;
-        const int64_t k = (int64_t)p->bi[pe];
+        const int64_t k = (int64_t)__ldg(&p->bi[pe]);
         if (k < k0 || k >= k1) { len = 0; return; }
-        const int64_t a0 = (int64_t)p->ap[k], a1 = (int64_t)p->ap[k + 1];
-        beg = a0; len = (int)(a1 - a0); bv = p->bv[pe]; tag = pe;
+        const int64_t a0 = (int64_t)__ldg(&p->ap[k]), a1 = (int64_t)__ldg(&p->ap[k + 1]);
+        beg = a0; len = (int)(a1 - a0); bv = __ldg(&p->bv[pe]); tag = pe;
     }
-    __device__ __forceinline__ uint32_t row(int64_t q) const { return (uint32_t)p->ai[q]; }
-    __device__ __forceinline__ V val(int64_t q, V bv) const { return mul_v(p->av[q], bv); }
+    __device__ __forceinline__ uint32_t row(int64_t q) const { return (uint32_t)__ldg(&p->ai[q]); }
+    __device__ __forceinline__ V val(int64_t q, V bv) const { return mul_v(__ldg(&p->av[q]), bv); }
     // number of contributions (multiplications) of the column; warp-wide
     __device__ __forceinline__ int64_t flops() const {
         const int lane = threadIdx.x & 31;
@@ -208,14 +209,14 @@ template <class I, class V> struct SrcPanel {
     __device__ __forceinline__ int64_t nseg() const { return nb; }
     __device__ __forceinline__ void seg(int64_t e, int64_t &beg, int &len, V &bv, int64_t &tag) const {
         const int64_t pe = b0 + e;
-        const int64_t k = (int64_t)p->bi[pe];
+        const int64_t k = (int64_t)__ldg(&p->bi[pe]);
         if (k < k0 || k >= k1) { len = 0; return; }
         const int64_t idx = pk + k;
-        const int64_t s = idx ? ape[idx - 1] : 0;
-        beg = s; len = (int)(ape[idx] - s); bv = p->bv[pe]; tag = pe;
+        const int64_t s = idx ? __ldg(&ape[idx - 1]) : 0;
+        beg = s; len = (int)(__ldg(&ape[idx]) - s); bv = __ldg(&p->bv[pe]); tag = pe;
     }
-    __device__ __forceinline__ int lrow(int64_t q) const { return (int)apr[q]; }
-    __device__ __forceinline__ V val(int64_t q, V bv) const { return mul_v(apv[q], bv); }
+    __device__ __forceinline__ int lrow(int64_t q) const { return (int)__ldg(&apr[q]); }
+    __device__ __forceinline__ V val(int64_t q, V bv) const { return mul_v(__ldg(&apv[q]), bv); }
 };
 
 template <class I, class V> struct SrcPartsPanel {
@@ -307,7 +308,7 @@ template <class V> struct BlockShared {
 // Consecutive lanes read consecutive entries of a segment (coalesced). All
 // threads must call it; it ends with a __syncthreads.
 template <class Src, class Emit>
-__device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int, int,
+__device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short_seg, int,
                                            BlockShared<typename Src::Val> &sh) {
     using V = typename Src::Val;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -319,7 +320,16 @@ __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int, int,
         int len = 0;
         V bv = V(0);
         if (e < nseg) src.seg(e, beg, len, bv, tag);
-        // block scan of (nonempty << 40 | len): compacted slot and stream start
+        // short segments: each lane walks its own, in a warp-uniform loop
+        // bounded by the warp's longest short segment
+        {
+            const int mine = len <= short_seg ? len : 0;
+            const int wmax = __reduce_max_sync(SPG_FULL, (unsigned)mine);
+            for (int i = 0; i < wmax; ++i) emit(beg + i, bv, tag, i < mine);
+            if (len <= short_seg) len = 0;
+        }
+        // longer segments: block scan of (nonempty << 40 | len) gives the
+        // compacted slot and the start in the flattened product stream
         const int64_t key = ((int64_t)(len > 0) << 40) | (int64_t)len;
         int64_t incl = warp_incl_scan(key);
         if (lane == 31) sh.red64[warp] = incl;
@@ -365,18 +375,18 @@ __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int, int,
                 int64_t qbase = sh.qb[s_lo];
                 V bvc = sh.bv[s_lo];
                 int64_t tagc = sh.tag[s_lo];
-                for (int64_t wb = p0; wb < p1; wb += 32) {
+                // lane assignment of the window starting at wb; advances s_lo
+                auto window = [&](int64_t wb, int64_t &q, V &bv, int64_t &tg, bool &valid) {
                     const int64_t t = wb + lane;
-                    const bool valid = t < p1;
-                    if (wb + 32 <= seg_end) {
-                        // the whole window lies in segment s_lo
-                        emit(qbase + t, bvc, tagc, valid);
+                    valid = t < p1;
+                    if (wb + 32 <= seg_end) {          // the window lies in segment s_lo
+                        q = qbase + t; bv = bvc; tg = tagc;
                         if (wb + 32 == seg_end && s_lo + 1 < nz) {
                             ++s_lo;
                             seg_end = (s_lo + 1 < nz) ? sh.start[s_lo + 1] : T;
                             qbase = sh.qb[s_lo]; bvc = sh.bv[s_lo]; tagc = sh.tag[s_lo];
                         }
-                        continue;
+                        return;
                     }
                     // the window crosses segment starts: lane l's segment is
                     // s_lo plus the number of starts at positions 1..l
@@ -389,11 +399,37 @@ __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int, int,
                     const unsigned M = __reduce_or_sync(SPG_FULL, bit);
                     const int sg = s_lo + __popc(M & (0xffffffffu >> (31 - lane)));
                     const int sgv = valid ? sg : s_lo;
-                    emit(sh.qb[sgv] + (valid ? t : sh.start[sgv]), sh.bv[sgv], sh.tag[sgv], valid);
+                    q = sh.qb[sgv] + (valid ? t : sh.start[sgv]);
+                    bv = sh.bv[sgv]; tg = sh.tag[sgv];
                     s_lo += __popc(M);
                     if (s_lo + 1 < nz && sh.start[s_lo + 1] == wb + 32) ++s_lo;
                     seg_end = (s_lo + 1 < nz) ? sh.start[s_lo + 1] : T;
                     qbase = sh.qb[s_lo]; bvc = sh.bv[s_lo]; tagc = sh.tag[s_lo];
+                };
+                for (int64_t wb = p0; wb < p1;) {
+                    if (wb + 128 <= seg_end && wb + 128 <= p1) {
+                        // four whole windows inside segment s_lo: independent
+                        // products back to back (their loads overlap)
+                        const int64_t q0 = qbase + wb + lane;
+                        emit(q0, bvc, tagc, true);
+                        emit(q0 + 32, bvc, tagc, true);
+                        emit(q0 + 64, bvc, tagc, true);
+                        emit(q0 + 96, bvc, tagc, true);
+                        wb += 128;
+                        if (wb == seg_end && s_lo + 1 < nz) {
+                            ++s_lo;
+                            seg_end = (s_lo + 1 < nz) ? sh.start[s_lo + 1] : T;
+                            qbase = sh.qb[s_lo]; bvc = sh.bv[s_lo]; tagc = sh.tag[s_lo];
+                        }
+                        continue;
+                    }
+                    int64_t q;
+                    V v;
+                    int64_t tg;
+                    bool ok;
+                    window(wb, q, v, tg, ok);
+                    emit(q, v, tg, ok);
+                    wb += 32;
                 }
             }
         }
@@ -614,26 +650,14 @@ __global__ void __launch_bounds__(1024, 1) k_sym_bitmap(typename Src::Args sa, T
         const int64_t rows = (mrows - r0) < c.Rs ? (mrows - r0) : c.Rs;
         const int nwords = (int)((rows + 31) >> 5);
         const bool filt = c.Q > 1;
-        // Lanes of a window often mark the same bitmap word (rows of one A
-        // column are clustered): a shuffle-based OR over lanes with equal
-        // words leaves one shared atomic per run of equal words.
         auto emit = [&](int64_t qq, V, int64_t, bool valid) {
-            const int lane = threadIdx.x & 31;
-            int64_t r = valid ? (int64_t)src.row(qq) : -1;
-            if (filt && r >= 0) {
+            if (!valid) return;
+            int64_t r = (int64_t)src.row(qq);
+            if (filt) {
                 r -= r0;
-                if (r >= rows) r = -1;
+                if (r < 0 || r >= rows) return;
             }
-            const unsigned w = r >= 0 ? (unsigned)(r >> 5) : 0x80000000u + lane;
-            unsigned b = r >= 0 ? 1u << (r & 31) : 0u;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned w2 = __shfl_down_sync(SPG_FULL, w, o);
-                const unsigned b2 = __shfl_down_sync(SPG_FULL, b, o);
-                if (lane + o < 32 && w2 == w) b |= b2;
-            }
-            const unsigned wprev = __shfl_up_sync(SPG_FULL, w, 1);
-            if (r >= 0 && (lane == 0 || wprev != w)) atomicOr(&bm[w], b);
+            atomicOr(&bm[r >> 5], 1u << (r & 31));
         };
         block_walk(src, emit, c.short_seg, c.huge_seg, sh);
         const int h = c.heavy_ord[g];
@@ -881,6 +905,11 @@ __global__ void k_heavy_items(const int32_t *list, const int32_t *list_off, cons
                               int P, int dense_min, int mode, int64_t *ncount,
                               const int64_t *item_off, HeavyItem *items);
 
+// Panel-major item order (defined in util_kernels.cu).
+__global__ void k_items_by_panel(const HeavyItem *items, const int64_t *n_items_p, int mode,
+                                 int32_t *panel_cnt, int32_t *order);
+__global__ void k_small_excl_scan(int32_t *a, int P);
+
 // Range sources: the contributions of column g restricted to panels
 // [p0, p1). seg() yields segments; row(q, tag) is the global row.
 template <class I, class V> struct SrcPanelRange {
@@ -908,17 +937,17 @@ template <class I, class V> struct SrcPanelRange {
         const int64_t e = e2 / np;
         const int pp = p0 + (int)(e2 - e * np);
         const int64_t pe = b0 + e;
-        const int64_t k = (int64_t)p->bi[pe];
+        const int64_t k = (int64_t)__ldg(&p->bi[pe]);
         if (k < k0 || k >= k1) { len = 0; return; }
         const int64_t idx = (int64_t)pp * ka + k;
-        const int64_t s = idx ? ape[idx - 1] : 0;
-        beg = s; len = (int)(ape[idx] - s); bv = p->bv[pe];
+        const int64_t s = idx ? __ldg(&ape[idx - 1]) : 0;
+        beg = s; len = (int)(__ldg(&ape[idx]) - s); bv = __ldg(&p->bv[pe]);
         tag = (int64_t)pp << log2R;      // row base of the panel
     }
     __device__ __forceinline__ uint32_t row(int64_t q, int64_t tag) const {
-        return (uint32_t)(tag + apr[q]);
+        return (uint32_t)(tag + __ldg(&apr[q]));
     }
-    __device__ __forceinline__ V val(int64_t q, V bv) const { return mul_v(apv[q], bv); }
+    __device__ __forceinline__ V val(int64_t q, V bv) const { return mul_v(__ldg(&apv[q]), bv); }
 };
 
 template <class I, class V> struct SrcPartsRange {
@@ -961,20 +990,19 @@ template <class I, class V> struct SrcPartsRange {
 
 template <class DSrc>
 __global__ void __launch_bounds__(512, 2) k_num_heavy(typename DSrc::Args sa, TierCommon c,
-                                                      const HeavyItem *items, const int64_t *nitems_p,
+                                                      const HeavyItem *items, const int32_t *order,
+                                                      const int64_t *nitems_p,
                                                       typename DSrc::Idx *out_rows,
                                                       typename DSrc::Val *out_vals) {
     using V = typename DSrc::Val;
     using I = typename DSrc::Idx;
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = 1 << c.log2R;
-    constexpr int T = 1 << kRangeLog2T;
-    // dense view: acc[R] values + flg[R] bytes; hash view: vals[T] + keys[T]
+    // dense view: acc[R] values + flg[R] bytes; hash view (same memory):
+    // vals[Ti] + keys[Ti] with Ti <= 2^kRangeLog2T sized per item
     V *acc = reinterpret_cast<V *>(smem);
     unsigned char *flg = smem + sizeof(V) * R;
     uint32_t *flg4 = reinterpret_cast<uint32_t *>(flg);
-    V *hv = reinterpret_cast<V *>(smem);
-    uint32_t *hk = reinterpret_cast<uint32_t *>(smem + sizeof(V) * T);
     __shared__ BlockShared<V> sh;
     for (int r = threadIdx.x; r < R; r += blockDim.x) { acc[r] = V(0); flg[r] = 0; }
     if (threadIdx.x == 0) sh.pos = 0;
@@ -982,15 +1010,31 @@ __global__ void __launch_bounds__(512, 2) k_num_heavy(typename DSrc::Args sa, Ti
     const int64_t nitems = *nitems_p;
     const int lane = threadIdx.x & 31;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const HeavyItem item = items[it];
+        const HeavyItem item = items[order[it]];
         const int64_t g = item.g;
         if (g < c.c_lo || g >= c.c_hi) continue;
-        const bool dense = item.cnt < 0;
+        bool dense = item.cnt < 0;
         const int p0 = item.p0;
         const int p1 = item.p1;
-        const int mycnt = dense ? -item.cnt : item.cnt;
-        const int64_t out0 = c.colptr[g] - c.out_base + item.off;
+        int mycnt = dense ? -item.cnt : item.cnt;
+        int64_t ioff = item.off;
         const int h = c.heavy_ord[g];
+        if (c.item_counts_from_pcnt) {
+            // a k-stage: the same panel ranges, this stage's counts
+            const int32_t *pc = c.pcnt_in + (int64_t)h * c.P;
+            int below = 0, in = 0;
+            for (int pp = lane; pp < p1; pp += 32) {
+                const int x = pc[pp];
+                if (pp < p0) below += x; else in += x;
+            }
+            below = warp_sum(below);
+            in = warp_sum(in);
+            mycnt = in;
+            ioff = below;
+            dense = (p1 - p0 == 1);
+            if (mycnt == 0) continue;
+        }
+        const int64_t out0 = c.colptr[g] - c.out_base + ioff;
         DSrc src;
         src.open(sa, c, g, p0, p1, h);
         if (dense) {
@@ -1031,20 +1075,26 @@ __global__ void __launch_bounds__(512, 2) k_num_heavy(typename DSrc::Args sa, Ti
                 }
             }
         } else {
-            for (int s = threadIdx.x; s < T; s += blockDim.x) { hk[s] = kEmpty; hv[s] = V(0); }
+            // table sized to the item: the next power of two >= 2 * count
+            int lt = 6;
+            while ((1 << lt) < 2 * mycnt && lt < kRangeLog2T) ++lt;
+            const int Ti = 1 << lt;
+            V *tv = reinterpret_cast<V *>(smem);
+            uint32_t *tk = reinterpret_cast<uint32_t *>(smem + sizeof(V) * Ti);
+            for (int s = threadIdx.x; s < Ti; s += blockDim.x) { tk[s] = kEmpty; tv[s] = V(0); }
             __syncthreads();
             auto emit = [&](int64_t q, V bv, int64_t tag, bool valid) {
                 if (!valid) return;
                 const uint32_t gr = src.row(q, tag);
                 if (gr == kEmpty) return;
                 bool nw;
-                const int hh = hash_insert(hk, kRangeLog2T, gr, nw, c.err);
-                if (hh >= 0) atomic_add_v(&hv[hh], src.val(q, bv));
+                const int hh = hash_insert(tk, lt, gr, nw, c.err);
+                if (hh >= 0) atomic_add_v(&tv[hh], src.val(q, bv));
             };
             block_walk(src, emit, c.short_seg, c.huge_seg, sh);
-            for (int s0 = 0; s0 < T; s0 += blockDim.x) {
+            for (int s0 = 0; s0 < Ti; s0 += blockDim.x) {
                 const int s = s0 + threadIdx.x;
-                const uint32_t key = s < T ? hk[s] : kEmpty;
+                const uint32_t key = s < Ti ? tk[s] : kEmpty;
                 const bool occ = key != kEmpty;
                 const unsigned bal = __ballot_sync(SPG_FULL, occ);
                 int wbase = 0;
@@ -1054,13 +1104,15 @@ __global__ void __launch_bounds__(512, 2) k_num_heavy(typename DSrc::Args sa, Ti
                     const int o = wbase + __popc(bal & ((1u << lane) - 1u));
                     if (o < mycnt) {
                         out_rows[out0 + o] = (I)key;
-                        out_vals[out0 + o] = hv[s];
+                        out_vals[out0 + o] = tv[s];
                     }
                 }
             }
             __syncthreads();
-            // the dense view shares this memory: restore its zero state
-            for (int r = threadIdx.x; r < R; r += blockDim.x) { acc[r] = V(0); flg[r] = 0; }
+            // the dense view shares this memory: zero the bytes the table used
+            const int used4 = (int)((sizeof(V) + 4) * Ti / 4);
+            uint32_t *z = reinterpret_cast<uint32_t *>(smem);
+            for (int w = threadIdx.x; w < used4; w += blockDim.x) z[w] = 0u;
         }
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -46,7 +46,7 @@ struct HostBuf {
 struct Tuning {
     int hash_cap_max = 8192;
     int log2R = 15;          // dense panel rows (set per value type at plan time)
-    int short_seg = 8;
+    int short_seg = 1;
     int huge_seg = 4096;
     int block_threads = 0;   // 0: per-tier default
 };
@@ -138,7 +138,7 @@ struct PlanState {
     DevBuf ap_end, ap_row, ap_val;
     DevBuf stage_cnt, stage_colptr, stage_pcnt, drows, dvals, parts_tab;  // k-split
     DevBuf merge_tmp;
-    DevBuf items, item_cnt, item_off;    // heavy work items (dense panels / hash ranges)
+    DevBuf items, item_cnt, item_off, item_order;  // heavy work items (dense panels / hash ranges)
     int64_t n_items = 0;
     HostBuf h_colptr, h_small, h_stage_colptr, h_parts;
     std::vector<DevBuf> ring_col, ring_row, ring_val;   // spgemm_run_batched device ring

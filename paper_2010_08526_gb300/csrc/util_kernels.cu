@@ -108,6 +108,42 @@ __global__ void k_heavy_items(const int32_t *list, const int32_t *list_off, cons
     if (!mode) ncount[h] = n_items;
 }
 
+// Panel-major order of the heavy items (counting sort by first panel), so
+// that the CTAs running at the same time read the same panel of A and of the
+// panel offsets from L2. mode 0: histogram; mode 1: scatter.
+__global__ void k_items_by_panel(const HeavyItem *items, const int64_t *n_items_p, int mode,
+                                 int32_t *panel_cnt, int32_t *order) {
+    const int64_t n = *n_items_p;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int p = items[i].p0;
+        if (mode == 0) atomicAdd(&panel_cnt[p], 1);
+        else order[atomicAdd(&panel_cnt[p], 1)] = (int32_t)i;
+    }
+}
+
+// exclusive scan of P ints in place (one CTA)
+__global__ void k_small_excl_scan(int32_t *a, int P) {
+    __shared__ int32_t s[1024];
+    int carry = 0;
+    for (int base = 0; base < P; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < P ? a[i] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            const int t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < P) a[i] = carry + s[threadIdx.x] - v;
+        const int tot = s[blockDim.x - 1];
+        __syncthreads();
+        carry += tot;
+    }
+}
+
 // ---- exclusive scan of int64 (three phases, all on the device) ------------
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;
