@@ -256,7 +256,7 @@ def run_gpu(args):
     achieved = bytes_per_launch / (dense_ms / 1e3) / 1e9 if dense_ms > 0 else 0.0
     phase_ms = {k: round(v / args.steps, 3) for k, v in stats["ms"].items() if v}
     traffic = None
-    tf = os.path.join(ROOT, "profiles", "traffic_num_dense.txt")
+    tf = os.path.join(ROOT, "profiles", "traffic_num_heavy.txt")
     if os.path.exists(tf):
         for line in open(tf):
             if line.startswith("bytes_per_full_launch"):

@@ -19,13 +19,15 @@ enum : int {
     kErrIndex = 4,        // an index outside its array was met (corrupt input)
 };
 
-// Number of column tiers. Tier 0: empty column. Tiers 1..2: one warp per
-// column with a 2*cap-slot table. Tiers 3..8: one CTA per column, table of
-// 2*cap slots (cap = 256 .. 8192). Tiers 9..15: heavy columns (dense
-// accumulators), split by log2 of their size so that the largest run first.
+// Number of column tiers. Tier 0: empty column. Tiers 1..4: one warp per
+// column with a 2*cap-slot table (cap 32, 128, 256, 512). Tiers 5..8: one CTA
+// per column, table of 2*cap slots (cap 1024 .. 8192). Tiers 9..15: heavy
+// columns (dense accumulators), split by log2 of their size so that the
+// largest run first.
 constexpr int kTiers = 16;
 constexpr int kHeavyTier0 = 9;
-constexpr int kWarpTierCap[3] = {0, 32, 128};
+// tiers 1..kWarpTiers run one warp per column (warp-private tables)
+constexpr int kWarpTiers = 4;
 __host__ __device__ constexpr int tier_cap(int t) {
     // capacity (max distinct rows) of hash tiers 1..8
     return t == 1 ? 32 : t == 2 ? 128 : (128 << (t - 2));

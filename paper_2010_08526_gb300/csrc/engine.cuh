@@ -139,6 +139,14 @@ template <class I, class V> struct Engine : EngineBase {
         set_smem(k_num_dense<SrcPanel<I, V>>, mx);
         set_smem(k_num_dense<SrcPartsPanel<I, V>>, mx);
         set_smem(k_bwd_dense<I, V>, mx);
+        set_smem(k_sym_warp<SrcGemm<I, V>, 1024>, mx);
+        set_smem(k_sym_warp<SrcParts<I, V>, 1024>, mx);
+        set_smem(k_num_warp<SrcGemm<I, V>, 512>, mx);
+        set_smem(k_num_warp<SrcGemm<I, V>, 1024>, mx);
+        set_smem(k_num_warp<SrcParts<I, V>, 512>, mx);
+        set_smem(k_num_warp<SrcParts<I, V>, 1024>, mx);
+        set_smem(k_bwd_warp<I, V, 512>, mx);
+        set_smem(k_bwd_warp<I, V, 1024>, mx);
         set_smem(k_num_heavy<SrcPanelRange<I, V>>, mx);
         set_smem(k_num_heavy<SrcPartsRange<I, V>>, mx);
         (void)sv;
@@ -152,11 +160,18 @@ template <class I, class V> struct Engine : EngineBase {
                                 int count, cudaStream_t st) {
         c.tier = t;
         const int T = 2 * tier_cap(t);
-        if (t <= 2) {
-            const int want = count < 0 ? cx.nsm * 8 : (count + 7) / 8;
-            const int blocks = std::max(1, std::min(want, cx.nsm * 8));
-            if (T == 64) k_sym_warp<Src, 64><<<blocks, 256, 0, st>>>(sa, c);
-            else k_sym_warp<Src, 256><<<blocks, 256, 0, st>>>(sa, c);
+        if (t <= kWarpTiers) {
+            // one warp per column, 8 warps per CTA, warp-private tables
+            const int smem = 8 * T * 4;
+            const int per_sm = std::max(1, std::min(8, (228 * 1024) / (smem + 1024)));
+            const int want = count < 0 ? cx.nsm * per_sm : (count + 7) / 8;
+            const int blocks = std::max(1, std::min(want, cx.nsm * per_sm));
+            switch (T) {
+                case 64: k_sym_warp<Src, 64><<<blocks, 256, smem, st>>>(sa, c); break;
+                case 256: k_sym_warp<Src, 256><<<blocks, 256, smem, st>>>(sa, c); break;
+                case 512: k_sym_warp<Src, 512><<<blocks, 256, smem, st>>>(sa, c); break;
+                default: k_sym_warp<Src, 1024><<<blocks, 256, smem, st>>>(sa, c); break;
+            }
             return;
         }
         const int thr = block_tier_threads(T, cx.tun);
@@ -179,11 +194,17 @@ template <class I, class V> struct Engine : EngineBase {
                                 int count, I *rows, V *vals, cudaStream_t st) {
         c.tier = t;
         const int T = 2 * tier_cap(t);
-        if (t <= 2) {
-            const int want = count < 0 ? cx.nsm * 8 : (count + 7) / 8;
-            const int blocks = std::max(1, std::min(want, cx.nsm * 8));
-            if (T == 64) k_num_warp<Src, 64><<<blocks, 256, 0, st>>>(sa, c, rows, vals);
-            else k_num_warp<Src, 256><<<blocks, 256, 0, st>>>(sa, c, rows, vals);
+        if (t <= kWarpTiers) {
+            const int smem = 8 * T * (int)(4 + sizeof(V));
+            const int per_sm = std::max(1, std::min(8, (228 * 1024) / (smem + 1024)));
+            const int want = count < 0 ? cx.nsm * per_sm : (count + 7) / 8;
+            const int blocks = std::max(1, std::min(want, cx.nsm * per_sm));
+            switch (T) {
+                case 64: k_num_warp<Src, 64><<<blocks, 256, smem, st>>>(sa, c, rows, vals); break;
+                case 256: k_num_warp<Src, 256><<<blocks, 256, smem, st>>>(sa, c, rows, vals); break;
+                case 512: k_num_warp<Src, 512><<<blocks, 256, smem, st>>>(sa, c, rows, vals); break;
+                default: k_num_warp<Src, 1024><<<blocks, 256, smem, st>>>(sa, c, rows, vals); break;
+            }
             return;
         }
         const int thr = block_tier_threads(T, cx.tun);
@@ -757,10 +778,16 @@ template <class I, class V> struct Engine : EngineBase {
             if (!hist[t]) continue;
             c.tier = t;
             const int T = 2 * tier_cap(t);
-            if (t <= 2) {
-                const int blocks = std::max(1, std::min((hist[t] + 7) / 8, cx.nsm * 8));
-                if (T == 64) k_bwd_warp<I, V, 64><<<blocks, 256, 0, st>>>(ga, c);
-                else k_bwd_warp<I, V, 256><<<blocks, 256, 0, st>>>(ga, c);
+            if (t <= kWarpTiers) {
+                const int smem = 8 * T * (int)(4 + sizeof(V));
+                const int per_sm = std::max(1, std::min(8, (228 * 1024) / (smem + 1024)));
+                const int blocks = std::max(1, std::min((hist[t] + 7) / 8, cx.nsm * per_sm));
+                switch (T) {
+                    case 64: k_bwd_warp<I, V, 64><<<blocks, 256, smem, st>>>(ga, c); break;
+                    case 256: k_bwd_warp<I, V, 256><<<blocks, 256, smem, st>>>(ga, c); break;
+                    case 512: k_bwd_warp<I, V, 512><<<blocks, 256, smem, st>>>(ga, c); break;
+                    default: k_bwd_warp<I, V, 1024><<<blocks, 256, smem, st>>>(ga, c); break;
+                }
                 continue;
             }
             const int thr = block_tier_threads(T, cx.tun);

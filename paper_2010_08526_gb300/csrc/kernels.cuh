@@ -14,8 +14,8 @@
 //   SrcPartsPanel -- the same restricted to one row panel, through per-panel
 //                    offsets of panel-grouped partial columns, or by filtering.
 // Columns are put in tiers by the number of distinct rows they can hold:
-//   warp tiers  : one warp per column, 2*cap-slot hash table (cap 32, 128);
-//   block tiers : one CTA per column, 2*cap-slot hash table (cap 256..8192);
+//   warp tiers  : one warp per column, 2*cap-slot hash table (cap 32..512);
+//   block tiers : one CTA per column, 2*cap-slot hash table (cap 1024..8192);
 //   heavy tier  : symbolic -- a shared-memory bitmap over up to ~1.5M rows;
 //                 numeric  -- dense accumulation of one row panel in shared
 //                 memory per CTA.
@@ -563,9 +563,9 @@ template <class Src, int T>
 __global__ void __launch_bounds__(256) k_sym_warp(typename Src::Args sa, TierCommon c) {
     constexpr int LOG2T = Log2<T>::v;
     using V = typename Src::Val;
-    __shared__ uint32_t s_keys[8][T];
+    extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *keys = s_keys[warp];
+    uint32_t *keys = reinterpret_cast<uint32_t *>(smem) + warp * T;
     const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
     const int nwarps = gridDim.x * 8;
     for (int it = lo + blockIdx.x * 8 + warp; it < hi; it += nwarps) {
@@ -694,11 +694,10 @@ __global__ void __launch_bounds__(256) k_num_warp(typename Src::Args sa, TierCom
     constexpr int LOG2T = Log2<T>::v;
     using V = typename Src::Val;
     using I = typename Src::Idx;
-    __shared__ uint32_t s_keys[8][T];
-    __shared__ V s_vals[8][T];
+    extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *keys = s_keys[warp];
-    V *vals = s_vals[warp];
+    V *vals = reinterpret_cast<V *>(smem) + warp * T;
+    uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * 8 * T) + warp * T;
     const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
     const int nwarps = gridDim.x * 8;
     for (int it = lo + blockIdx.x * 8 + warp; it < hi; it += nwarps) {
@@ -1229,11 +1228,10 @@ __global__ void k_bwd_block(GradArgs<I, V> a, TierCommon c) {
 template <class I, class V, int T>
 __global__ void __launch_bounds__(256) k_bwd_warp(GradArgs<I, V> a, TierCommon c) {
     constexpr int LOG2T = Log2<T>::v;
-    __shared__ uint32_t s_keys[8][T];
-    __shared__ V s_vals[8][T];
+    extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *keys = s_keys[warp];
-    V *gv = s_vals[warp];
+    V *gv = reinterpret_cast<V *>(smem) + warp * T;
+    uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * 8 * T) + warp * T;
     const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
     const int nwarps = gridDim.x * 8;
     for (int it = lo + blockIdx.x * 8 + warp; it < hi; it += nwarps) {
