@@ -384,11 +384,17 @@ def run_gpu(args):
 def bench_multi(spg, torch, args):
     """512 uneven G(n,p) products (int64 ones semiring): one CUDA-graph
     launch of the device-driven multi-problem pass vs 512 plain plans."""
+    from paper_2010_08526_gb300 import autotune
     n = 512 if not args.small_extras else 64
     probs = W.config4(count=n, nmax=200000 if not args.small_extras else 20000)
     dev = [spg.Csc.from_host(p) for p in probs]
     flops = sum(int(flops_host(p).sum()) for p in probs)
-    M = spg.Multi(dev, dev)
+    # bin thresholds / table sizes / CTA shapes picked by the autotuner on the
+    # first 64 problems
+    cands = [spg.Tuning(hash_max_cap=cap, block_tier_threads=t)
+             for cap in (2048, 8192) for t in (0, 256)]
+    best, trials = autotune.tune_multi(dev[:64], dev[:64], cands, reps=2)
+    M = spg.Multi(dev, dev, tuning=best)
     M.run(use_graph=True)
     torch.cuda.synchronize()
     reps = 3
@@ -411,7 +417,8 @@ def bench_multi(spg, torch, args):
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
     return {"problems": n, "flops": flops, "multi_ms": t_multi * 1e3, "plain_ms": t_plain * 1e3,
-            "speedup": t_plain / t_multi, "multi_gflops": 2 * flops / t_multi / 1e9}
+            "speedup": t_plain / t_multi, "multi_gflops": 2 * flops / t_multi / 1e9,
+            "tuning": autotune.describe([(best, 0.0)])[0], "autotune_trials": autotune.describe(trials)}
 
 
 def bench_fwdbwd(spg, torch, args):

@@ -147,8 +147,10 @@ template <class I, class V> struct Engine : EngineBase {
         set_smem(k_num_warp<SrcParts<I, V>, 1024>, mx);
         set_smem(k_bwd_warp<I, V, 512>, mx);
         set_smem(k_bwd_warp<I, V, 1024>, mx);
-        set_smem(k_num_heavy<SrcPanelRange<I, V>>, mx);
-        set_smem(k_num_heavy<SrcPartsRange<I, V>>, mx);
+        set_smem(k_num_heavy<SrcPanelRange<I, V>, 2>, mx);
+        set_smem(k_num_heavy<SrcPartsRange<I, V>, 2>, mx);
+        set_smem(k_num_heavy<SrcPanelRange<I, V>, 3>, mx);
+        set_smem(k_num_heavy<SrcPartsRange<I, V>, 3>, mx);
         (void)sv;
         done = true;
     }
@@ -227,8 +229,18 @@ template <class I, class V> struct Engine : EngineBase {
         return R * (int)sizeof(V) + R;
     }
 
+    // largest hash-range item (output rows) whose table (2x slots) fits the
+    // memory of a dense item
+    static int range_cap(const Ctx &cx) {
+        const int R = 1 << cx.tun.log2R;
+        const int fit = (int)((int64_t)R * (sizeof(V) + 1) / (sizeof(V) + 4) / 2);
+        int cap = 64;
+        while (cap * 2 <= fit && cap * 2 <= kRangeCap) cap *= 2;
+        return cap;
+    }
+
     static int heavy_smem(const Ctx &cx) {
-        const int hs = (1 << kRangeLog2T) * (int)(sizeof(V) + 4);
+        const int hs = 2 * range_cap(cx) * (int)(sizeof(V) + 4);
         return std::max(dense_smem(cx), hs);
     }
 
@@ -248,8 +260,9 @@ template <class I, class V> struct Engine : EngineBase {
         const int R = 1 << cx.tun.log2R;
         const int dmin = std::max(1, R / 8);
         const unsigned nb = (unsigned)((nheavy + 255) / 256);
+        const int rcap = range_cap(cx);
         k_heavy_items<<<nb, 256, 0, st>>>(sym_list, sym_off, sel, cx.tun.hash_cap_max, 0, n, pcnt, cx.P,
-                                          dmin, 0, icnt.as<int64_t>(), nullptr, nullptr);
+                                          dmin, rcap, 0, icnt.as<int64_t>(), nullptr, nullptr);
         SPG_CK(exclusive_scan_i64(icnt.as<int64_t>(), nheavy, ioff.as<int64_t>(),
                                   scan_part.as<int64_t>(), 1, st));
         int64_t total = 0;
@@ -259,7 +272,7 @@ template <class I, class V> struct Engine : EngineBase {
         std::memcpy(&total, cx.h_small + 256, sizeof(int64_t));
         SPG_CK(items.ensure(sizeof(HeavyItem) * (size_t)(total + 1)));
         k_heavy_items<<<nb, 256, 0, st>>>(sym_list, sym_off, sel, cx.tun.hash_cap_max, 0, n, pcnt, cx.P,
-                                          dmin, 1, nullptr, ioff.as<int64_t>(), items.as<HeavyItem>());
+                                          dmin, rcap, 1, nullptr, ioff.as<int64_t>(), items.as<HeavyItem>());
         // panel-major processing order: item indices sorted by first panel,
         // stored after the items (icnt is reused for the panel histogram)
         SPG_CK(order.ensure(sizeof(int32_t) * (size_t)(total + 1)));
@@ -383,14 +396,22 @@ template <class I, class V> struct Engine : EngineBase {
             c.pcnt_in = pcnt_in;
             c.c_lo = c_lo; c.c_hi = c_hi;
             c.item_counts_from_pcnt = cx.stage_items ? 1 : 0;
+            c.range_cap = range_cap(cx);
             if constexpr (!std::is_same<RSrc, DSrc>::value) {
               if (items) {
+                // 512-thread CTAs; 3 per SM when the item memory allows it
+                // (registers are then capped at 42 per thread), else 2
                 const int smem = heavy_smem(cx);
-                const int per_sm = std::max(1, std::min(2, (228 * 1024) / (smem + 34 * 1024)));
+                const int stat = (int)sizeof(BlockShared<V, 512>) + 256;
+                const int per_sm = (3 * (smem + stat) <= 227 * 1024) ? 3 : 2;
                 const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * per_sm));
                 const int td = cx.tbegin(cx.ph_dense, st);
-                k_num_heavy<RSrc><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items_dev,
-                                                             o.rows, o.vals);
+                if (per_sm == 3)
+                    k_num_heavy<RSrc, 3><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items_dev,
+                                                                    o.rows, o.vals);
+                else
+                    k_num_heavy<RSrc, 2><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items_dev,
+                                                                    o.rows, o.vals);
                 cx.tend(td, st);
                 cx.launched();
                 SPG_CK(cudaGetLastError());

@@ -83,6 +83,7 @@ struct TierCommon {
     int Q;                   // symbolic panels per column
     int64_t c_lo, c_hi;      // global column range (dense items)
     int item_counts_from_pcnt; // heavy items: take count / offset from pcnt_in (a k-stage)
+    int range_cap;             // heavy hash items: at most this many output rows
 };
 
 template <class I, class V> struct GemmArgs {
@@ -286,11 +287,11 @@ constexpr int kMaxBlock = 1024;
 
 // Per-CTA scratch of the load-balanced walk: the non-empty segments of the
 // current chunk, compacted, with their start in the flattened product stream.
-template <class V> struct BlockShared {
-    int64_t start[kMaxBlock + 1];
-    int64_t qb[kMaxBlock];     // beg - start: entry index = qb[s] + stream position
-    int64_t tag[kMaxBlock];
-    V bv[kMaxBlock];
+template <class V, int MB = kMaxBlock> struct BlockShared {
+    int64_t start[MB + 1];
+    int64_t qb[MB];            // beg - start: entry index = qb[s] + stream position
+    int64_t tag[MB];
+    V bv[MB];
     int64_t red64[33];
     int nz;
     int pos;
@@ -307,9 +308,9 @@ template <class V> struct BlockShared {
 // finds its segment from a bitmask of the segment starts inside the window.
 // Consecutive lanes read consecutive entries of a segment (coalesced). All
 // threads must call it; it ends with a __syncthreads.
-template <class Src, class Emit>
+template <class Src, class Emit, int MB>
 __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short_seg, int,
-                                           BlockShared<typename Src::Val> &sh) {
+                                           BlockShared<typename Src::Val, MB> &sh) {
     using V = typename Src::Val;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
@@ -901,7 +902,7 @@ struct HeavyItem {
 // item_off[h] (exclusive scan of the counts).
 __global__ void k_heavy_items(const int32_t *list, const int32_t *list_off, const int64_t *sel,
                               int hash_cap_max, int64_t c_lo, int64_t c_hi, const int32_t *pcnt,
-                              int P, int dense_min, int mode, int64_t *ncount,
+                              int P, int dense_min, int range_cap, int mode, int64_t *ncount,
                               const int64_t *item_off, HeavyItem *items);
 
 // Panel-major item order (defined in util_kernels.cu).
@@ -987,8 +988,8 @@ template <class I, class V> struct SrcPartsRange {
     __device__ __forceinline__ V val(int64_t q, V) const { return base.val(q, V(1)); }
 };
 
-template <class DSrc>
-__global__ void __launch_bounds__(512, 2) k_num_heavy(typename DSrc::Args sa, TierCommon c,
+template <class DSrc, int MINB>
+__global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa, TierCommon c,
                                                       const HeavyItem *items, const int32_t *order,
                                                       const int64_t *nitems_p,
                                                       typename DSrc::Idx *out_rows,
@@ -1002,7 +1003,7 @@ __global__ void __launch_bounds__(512, 2) k_num_heavy(typename DSrc::Args sa, Ti
     V *acc = reinterpret_cast<V *>(smem);
     unsigned char *flg = smem + sizeof(V) * R;
     uint32_t *flg4 = reinterpret_cast<uint32_t *>(flg);
-    __shared__ BlockShared<V> sh;
+    __shared__ BlockShared<V, 512> sh;
     for (int r = threadIdx.x; r < R; r += blockDim.x) { acc[r] = V(0); flg[r] = 0; }
     if (threadIdx.x == 0) sh.pos = 0;
     __syncthreads();
@@ -1076,7 +1077,7 @@ __global__ void __launch_bounds__(512, 2) k_num_heavy(typename DSrc::Args sa, Ti
         } else {
             // table sized to the item: the next power of two >= 2 * count
             int lt = 6;
-            while ((1 << lt) < 2 * mycnt && lt < kRangeLog2T) ++lt;
+            while ((1 << lt) < 2 * mycnt && (1 << lt) < 2 * c.range_cap) ++lt;
             const int Ti = 1 << lt;
             V *tv = reinterpret_cast<V *>(smem);
             uint32_t *tk = reinterpret_cast<uint32_t *>(smem + sizeof(V) * Ti);

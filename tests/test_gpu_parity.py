@@ -405,6 +405,19 @@ def test_autograd_function_fp64_finite_differences():
     plan.close()
 
 
+def test_autotuner_picks_a_working_candidate():
+    from paper_2010_08526_gb300 import autotune
+    A = skewed(3000, 3000, 131, hubs=2, hub_deg=1500)
+    Ad = to_dev(A)
+    cands = autotune.candidates(caps=(1024, 8192), panels=(8192, 16384), threads=(0, 256))
+    best, res = autotune.tune_plan(Ad, Ad, cands, reps=1)
+    assert best in [r[0] for r in res] and len(res) == len(cands)
+    check_product(A, A, "autotuned", tuning=best)
+    probs = [to_dev(p) for p in W.config4(count=6, nmax=3000)]
+    bm, rm = autotune.tune_multi(probs, probs, reps=1)
+    assert bm in [r[0] for r in rm]
+
+
 # ---------------------------------------------------------------- batched problems
 
 def test_multi_path_counting_exact():
