@@ -308,7 +308,14 @@ template <class V, int MB = kMaxBlock> struct BlockShared {
 // finds its segment from a bitmask of the segment starts inside the window.
 // Consecutive lanes read consecutive entries of a segment (coalesced). All
 // threads must call it; it ends with a __syncthreads.
-template <class Src, class Emit, int MB>
+//
+// U > 0 selects the batched form: the walker itself reads the entries
+// (src.row, src.val) of U windows at a time -- all U loads are issued before
+// the first one is used -- and calls emit(row, x) for each, row == kEmpty
+// for a lane without an entry. A shared-memory update consumes its load, and
+// a warp issues in order, so this keeps U gathers in flight per warp instead
+// of one.
+template <int U = 0, class Src, class Emit, int MB>
 __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short_seg, int,
                                            BlockShared<typename Src::Val, MB> &sh) {
     using V = typename Src::Val;
@@ -326,7 +333,16 @@ __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short
         {
             const int mine = len <= short_seg ? len : 0;
             const int wmax = __reduce_max_sync(SPG_FULL, (unsigned)mine);
-            for (int i = 0; i < wmax; ++i) emit(beg + i, bv, tag, i < mine);
+            for (int i = 0; i < wmax; ++i) {
+                if constexpr (U == 0) {
+                    emit(beg + i, bv, tag, i < mine);
+                } else {
+                    const bool v = i < mine;
+                    const uint32_t r = v ? src.row(beg + i, tag) : kEmpty;
+                    const V x = v ? src.val(beg + i, bv) : V(0);
+                    emit(r, x);
+                }
+            }
             if (len <= short_seg) len = 0;
         }
         // longer segments: block scan of (nonempty << 40 | len) gives the
@@ -407,6 +423,30 @@ __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short
                     seg_end = (s_lo + 1 < nz) ? sh.start[s_lo + 1] : T;
                     qbase = sh.qb[s_lo]; bvc = sh.bv[s_lo]; tagc = sh.tag[s_lo];
                 };
+                if constexpr (U > 0) {
+                    for (int64_t wb = p0; wb < p1; wb += 32 * U) {
+                        int64_t q[U], tg[U];
+                        V b[U];
+                        bool ok[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (wb + 32 * u < p1) {
+                                window(wb + 32 * u, q[u], b[u], tg[u], ok[u]);
+                            } else {
+                                q[u] = 0; tg[u] = 0; b[u] = V(0); ok[u] = false;
+                            }
+                        }
+                        uint32_t r[U];
+                        V x[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            r[u] = ok[u] ? src.row(q[u], tg[u]) : kEmpty;
+                            x[u] = ok[u] ? src.val(q[u], b[u]) : V(0);
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) emit(r[u], x[u]);
+                    }
+                } else
                 for (int64_t wb = p0; wb < p1;) {
                     if (wb + 128 <= seg_end && wb + 128 <= p1) {
                         // four whole windows inside segment s_lo: independent
@@ -988,6 +1028,9 @@ template <class I, class V> struct SrcPartsRange {
     __device__ __forceinline__ V val(int64_t q, V) const { return base.val(q, V(1)); }
 };
 
+// windows whose gathers a warp of the heavy kernel keeps in flight
+constexpr int kHeavyBatch = 4;
+
 template <class DSrc, int MINB>
 __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa, TierCommon c,
                                                       const HeavyItem *items, const int32_t *order,
@@ -1039,15 +1082,13 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
         src.open(sa, c, g, p0, p1, h);
         if (dense) {
             const int64_t rbase = (int64_t)p0 << c.log2R;
-            auto emit = [&](int64_t q, V bv, int64_t tag, bool valid) {
-                if (!valid) return;
-                const uint32_t gr = src.row(q, tag);
+            auto emit = [&](uint32_t gr, V x) {
                 if (gr == kEmpty) return;
                 const int r = (int)((int64_t)gr - rbase);
-                atomic_add_v(&acc[r], src.val(q, bv));
+                atomic_add_v(&acc[r], x);
                 flg[r] = 1;
             };
-            block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+            block_walk<kHeavyBatch>(src, emit, c.short_seg, c.huge_seg, sh);
             for (int w0 = 0; w0 < (R >> 2); w0 += blockDim.x) {
                 const int w = w0 + threadIdx.x;
                 const uint32_t x = w < (R >> 2) ? flg4[w] : 0u;
@@ -1083,15 +1124,13 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
             uint32_t *tk = reinterpret_cast<uint32_t *>(smem + sizeof(V) * Ti);
             for (int s = threadIdx.x; s < Ti; s += blockDim.x) { tk[s] = kEmpty; tv[s] = V(0); }
             __syncthreads();
-            auto emit = [&](int64_t q, V bv, int64_t tag, bool valid) {
-                if (!valid) return;
-                const uint32_t gr = src.row(q, tag);
+            auto emit = [&](uint32_t gr, V x) {
                 if (gr == kEmpty) return;
                 bool nw;
                 const int hh = hash_insert(tk, lt, gr, nw, c.err);
-                if (hh >= 0) atomic_add_v(&tv[hh], src.val(q, bv));
+                if (hh >= 0) atomic_add_v(&tv[hh], x);
             };
-            block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+            block_walk<kHeavyBatch>(src, emit, c.short_seg, c.huge_seg, sh);
             for (int s0 = 0; s0 < Ti; s0 += blockDim.x) {
                 const int s = s0 + threadIdx.x;
                 const uint32_t key = s < Ti ? tk[s] : kEmpty;
