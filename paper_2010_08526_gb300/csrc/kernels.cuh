@@ -309,12 +309,27 @@ template <class V, int MB = kMaxBlock> struct BlockShared {
 // Consecutive lanes read consecutive entries of a segment (coalesced). All
 // threads must call it; it ends with a __syncthreads.
 //
-// U > 0 selects the batched form: the walker itself reads the entries
-// (src.row, src.val) of U windows at a time -- all U loads are issued before
-// the first one is used -- and calls emit(row, x) for each, row == kEmpty
-// for a lane without an entry. A shared-memory update consumes its load, and
-// a warp issues in order, so this keeps U gathers in flight per warp instead
-// of one.
+// U > 0 selects the batched form, for emit = load_apply(load, apply):
+// load(q, bv, tag) reads entry q (global loads only) and apply(loaded, valid)
+// consumes it; the walker issues the loads of U windows before the first
+// apply. An update in shared memory consumes its load and a warp issues in
+// order, so this keeps U gathers in flight per warp instead of one.
+template <class Load, class Apply> struct LoadApply {
+    Load load;
+    Apply apply;
+};
+template <class Load, class Apply>
+__device__ __forceinline__ LoadApply<Load, Apply> load_apply(Load l, Apply a) {
+    return LoadApply<Load, Apply>{l, a};
+}
+// windows of gathers in flight per warp in the batched walks
+constexpr int kWalkBatch = 4;
+
+template <class V> struct RowVal {
+    uint32_t r;
+    V x;
+};
+
 template <int U = 0, class Src, class Emit, int MB>
 __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short_seg, int,
                                            BlockShared<typename Src::Val, MB> &sh) {
@@ -338,9 +353,9 @@ __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short
                     emit(beg + i, bv, tag, i < mine);
                 } else {
                     const bool v = i < mine;
-                    const uint32_t r = v ? src.row(beg + i, tag) : kEmpty;
-                    const V x = v ? src.val(beg + i, bv) : V(0);
-                    emit(r, x);
+                    decltype(emit.load(beg, bv, tag)) l{};
+                    if (v) l = emit.load(beg + i, bv, tag);
+                    emit.apply(l, v);
                 }
             }
             if (len <= short_seg) len = 0;
@@ -436,15 +451,14 @@ __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short
                                 q[u] = 0; tg[u] = 0; b[u] = V(0); ok[u] = false;
                             }
                         }
-                        uint32_t r[U];
-                        V x[U];
+                        decltype(emit.load(q[0], b[0], tg[0])) l[U];
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
-                            r[u] = ok[u] ? src.row(q[u], tg[u]) : kEmpty;
-                            x[u] = ok[u] ? src.val(q[u], b[u]) : V(0);
+                            l[u] = {};
+                            if (ok[u]) l[u] = emit.load(q[u], b[u], tg[u]);
                         }
 #pragma unroll
-                        for (int u = 0; u < U; ++u) emit(r[u], x[u]);
+                        for (int u = 0; u < U; ++u) emit.apply(l[u], ok[u]);
                     }
                 } else
                 for (int64_t wb = p0; wb < p1;) {
@@ -643,13 +657,14 @@ __global__ void k_sym_block(typename Src::Args sa, TierCommon c) {
         for (int s = threadIdx.x; s < T; s += blockDim.x) keys[s] = kEmpty;
         __syncthreads();
         int mine = 0;
-        auto emit = [&](int64_t q, V, int64_t, bool valid) {
-            if (!valid) return;
-            bool nw;
-            hash_insert(keys, LOG2T, src.row(q), nw, c.err);
-            mine += nw;
-        };
-        block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+        auto emit = load_apply([&](int64_t q, V, int64_t) { return src.row(q); },
+                               [&](uint32_t r, bool valid) {
+                                   if (!valid) return;
+                                   bool nw;
+                                   hash_insert(keys, LOG2T, r, nw, c.err);
+                                   mine += nw;
+                               });
+        block_walk<kWalkBatch>(src, emit, c.short_seg, c.huge_seg, sh);
         mine = warp_sum(mine);
         if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = mine;
         __syncthreads();
@@ -691,16 +706,17 @@ __global__ void __launch_bounds__(1024, 1) k_sym_bitmap(typename Src::Args sa, T
         const int64_t rows = (mrows - r0) < c.Rs ? (mrows - r0) : c.Rs;
         const int nwords = (int)((rows + 31) >> 5);
         const bool filt = c.Q > 1;
-        auto emit = [&](int64_t qq, V, int64_t, bool valid) {
-            if (!valid) return;
-            int64_t r = (int64_t)src.row(qq);
-            if (filt) {
-                r -= r0;
-                if (r < 0 || r >= rows) return;
-            }
-            atomicOr(&bm[r >> 5], 1u << (r & 31));
-        };
-        block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+        auto emit = load_apply([&](int64_t qq, V, int64_t) { return src.row(qq); },
+                               [&](uint32_t rr, bool valid) {
+                                   if (!valid) return;
+                                   int64_t r = (int64_t)rr;
+                                   if (filt) {
+                                       r -= r0;
+                                       if (r < 0 || r >= rows) return;
+                                   }
+                                   atomicOr(&bm[r >> 5], 1u << (r & 31));
+                               });
+        block_walk<kWalkBatch>(src, emit, c.short_seg, c.huge_seg, sh);
         const int h = c.heavy_ord[g];
         const int p0 = (int)(r0 >> c.log2R);
         const int np = (nwords + wordsR - 1) / wordsR;
@@ -795,13 +811,15 @@ __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::I
         src.open(sa, g);
         for (int s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = kEmpty; vals[s] = V(0); }
         __syncthreads();
-        auto emit = [&](int64_t q, V bv, int64_t, bool valid) {
-            if (!valid) return;
-            bool nw;
-            const int h = hash_insert(keys, LOG2T, src.row(q), nw, c.err);
-            if (h >= 0) atomic_add_v(&vals[h], src.val(q, bv));
-        };
-        block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+        auto emit = load_apply(
+            [&](int64_t q, V bv, int64_t) { return RowVal<V>{src.row(q), src.val(q, bv)}; },
+            [&](const RowVal<V> &e, bool valid) {
+                if (!valid) return;
+                bool nw;
+                const int h = hash_insert(keys, LOG2T, e.r, nw, c.err);
+                if (h >= 0) atomic_add_v(&vals[h], e.x);
+            });
+        block_walk<kWalkBatch>(src, emit, c.short_seg, c.huge_seg, sh);
         const int64_t out0 = c.colptr[g] - c.out_base;
         const int64_t want = c.colptr[g + 1] - c.colptr[g];
         for (int s0 = 0; s0 < T; s0 += blockDim.x) {
@@ -870,15 +888,15 @@ __global__ void __launch_bounds__(512, 2) k_num_dense(typename DSrc::Args sa, Ti
         const int64_t out0 = c.colptr[g] - c.out_base + below;
         DSrc src;
         src.open(sa, c, g, p, h);
-        auto emit = [&](int64_t q, V bv, int64_t, bool valid) {
-            if (!valid) return;
-            const int r = src.lrow(q);
-            if (r < 0) return;
-            atomic_add_v(&acc[r], src.val(q, bv));
-            flg[r] = 1;
-        };
-        (void)0;
-        block_walk(src, emit, c.short_seg, c.huge_seg, sh);
+        auto emit = load_apply(
+            [&](int64_t q, V bv, int64_t) { return RowVal<V>{(uint32_t)src.lrow(q), src.val(q, bv)}; },
+            [&](const RowVal<V> &e, bool valid) {
+                const int r = (int)e.r;
+                if (!valid || r < 0) return;
+                atomic_add_v(&acc[r], e.x);
+                flg[r] = 1;
+            });
+        block_walk<kWalkBatch>(src, emit, c.short_seg, c.huge_seg, sh);
         // compaction: each thread takes 4-row flag words; warp-aggregated slots
         const int64_t rbase = (int64_t)p << c.log2R;
         for (int w0 = 0; w0 < (R >> 2); w0 += blockDim.x) {
@@ -1082,12 +1100,14 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
         src.open(sa, c, g, p0, p1, h);
         if (dense) {
             const int64_t rbase = (int64_t)p0 << c.log2R;
-            auto emit = [&](uint32_t gr, V x) {
-                if (gr == kEmpty) return;
-                const int r = (int)((int64_t)gr - rbase);
-                atomic_add_v(&acc[r], x);
-                flg[r] = 1;
-            };
+            auto emit = load_apply(
+                [&](int64_t q, V bv, int64_t tag) { return RowVal<V>{src.row(q, tag), src.val(q, bv)}; },
+                [&](const RowVal<V> &e, bool valid) {
+                    if (!valid || e.r == kEmpty) return;
+                    const int r = (int)((int64_t)e.r - rbase);
+                    atomic_add_v(&acc[r], e.x);
+                    flg[r] = 1;
+                });
             block_walk<kHeavyBatch>(src, emit, c.short_seg, c.huge_seg, sh);
             for (int w0 = 0; w0 < (R >> 2); w0 += blockDim.x) {
                 const int w = w0 + threadIdx.x;
@@ -1124,12 +1144,14 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
             uint32_t *tk = reinterpret_cast<uint32_t *>(smem + sizeof(V) * Ti);
             for (int s = threadIdx.x; s < Ti; s += blockDim.x) { tk[s] = kEmpty; tv[s] = V(0); }
             __syncthreads();
-            auto emit = [&](uint32_t gr, V x) {
-                if (gr == kEmpty) return;
-                bool nw;
-                const int hh = hash_insert(tk, lt, gr, nw, c.err);
-                if (hh >= 0) atomic_add_v(&tv[hh], x);
-            };
+            auto emit = load_apply(
+                [&](int64_t q, V bv, int64_t tag) { return RowVal<V>{src.row(q, tag), src.val(q, bv)}; },
+                [&](const RowVal<V> &e, bool valid) {
+                    if (!valid || e.r == kEmpty) return;
+                    bool nw;
+                    const int hh = hash_insert(tk, lt, e.r, nw, c.err);
+                    if (hh >= 0) atomic_add_v(&tv[hh], e.x);
+                });
             block_walk<kHeavyBatch>(src, emit, c.short_seg, c.huge_seg, sh);
             for (int s0 = 0; s0 < Ti; s0 += blockDim.x) {
                 const int s = s0 + threadIdx.x;
