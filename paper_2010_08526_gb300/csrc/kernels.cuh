@@ -317,10 +317,33 @@ template <class V, int MB = kMaxBlock> struct BlockShared {
 template <class Load, class Apply> struct LoadApply {
     Load load;
     Apply apply;
+    // the entries of the U windows of a batch, in order
+    template <int U, class L>
+    __device__ __forceinline__ void apply_all(const L (&l)[U], const bool (&ok)[U]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) apply(l[u], ok[u]);
+    }
 };
 template <class Load, class Apply>
 __device__ __forceinline__ LoadApply<Load, Apply> load_apply(Load l, Apply a) {
     return LoadApply<Load, Apply>{l, a};
+}
+// The same with one call for a whole batch: all(l, ok) takes the arrays of
+// the U windows (a lane's U entries), so their updates can overlap.
+template <class Load, class All> struct LoadApplyAll {
+    Load load;
+    All all;
+    template <int U, class L>
+    __device__ __forceinline__ void apply_all(const L (&l)[U], const bool (&ok)[U]) { all(l, ok); }
+    template <class L> __device__ __forceinline__ void apply(const L &x, bool v) {
+        const L a[1] = {x};
+        const bool o[1] = {v};
+        all(a, o);
+    }
+};
+template <class Load, class All>
+__device__ __forceinline__ LoadApplyAll<Load, All> load_apply_all(Load l, All a) {
+    return LoadApplyAll<Load, All>{l, a};
 }
 // windows of gathers in flight per warp in the batched walks
 constexpr int kWalkBatch = 4;
@@ -457,8 +480,7 @@ __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short
                             l[u] = {};
                             if (ok[u]) l[u] = emit.load(q[u], b[u], tg[u]);
                         }
-#pragma unroll
-                        for (int u = 0; u < U; ++u) emit.apply(l[u], ok[u]);
+                        emit.apply_all(l, ok);
                     }
                 } else
                 for (int64_t wb = p0; wb < p1;) {
@@ -531,6 +553,44 @@ __device__ __forceinline__ int hash_insert(uint32_t *keys, int log2T, uint32_t k
     }
     atomicOr(err, kErrProbe);
     return -1;
+}
+
+// hash_insert for a lane's U keys at once (kEmpty = no key): every round
+// issues the probe loads of all pending keys, then the CAS of those that met
+// an empty slot, then resolves them, so the U probe chains overlap instead of
+// running one after another. slot[u] = the key's slot, -1 for no key (or a
+// full table, which sets kErrProbe).
+template <int U>
+__device__ __forceinline__ void hash_insert_all(uint32_t *keys, int log2T, const uint32_t (&key)[U],
+                                                int (&slot)[U], int *err) {
+    const uint32_t mask = (1u << log2T) - 1u;
+    uint32_t h[U];
+    unsigned pending = 0u;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        slot[u] = -1;
+        h[u] = hash_slot(key[u], log2T);
+        if (key[u] != kEmpty) pending |= 1u << u;
+    }
+    for (uint32_t probe = 0; pending && probe <= mask; ++probe) {
+        uint32_t cur[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) cur[u] = ((pending >> u) & 1u) ? keys[h[u]] : 0u;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (((pending >> u) & 1u) && cur[u] == kEmpty) cur[u] = atomicCAS(&keys[h[u]], kEmpty, key[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!((pending >> u) & 1u)) continue;
+            if (cur[u] == kEmpty || cur[u] == key[u]) {
+                slot[u] = (int)h[u];
+                pending &= ~(1u << u);
+            } else {
+                h[u] = (h[u] + 1u) & mask;
+            }
+        }
+    }
+    if (pending) atomicOr(err, kErrProbe);
 }
 
 // Lookup only; -1 when absent.
@@ -1144,13 +1204,18 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
             uint32_t *tk = reinterpret_cast<uint32_t *>(smem + sizeof(V) * Ti);
             for (int s = threadIdx.x; s < Ti; s += blockDim.x) { tk[s] = kEmpty; tv[s] = V(0); }
             __syncthreads();
-            auto emit = load_apply(
+            auto emit = load_apply_all(
                 [&](int64_t q, V bv, int64_t tag) { return RowVal<V>{src.row(q, tag), src.val(q, bv)}; },
-                [&](const RowVal<V> &e, bool valid) {
-                    if (!valid || e.r == kEmpty) return;
-                    bool nw;
-                    const int hh = hash_insert(tk, lt, e.r, nw, c.err);
-                    if (hh >= 0) atomic_add_v(&tv[hh], e.x);
+                [&](const auto &e, const auto &ok) {
+                    constexpr int UU = sizeof(ok) / sizeof(ok[0]);
+                    uint32_t key[UU];
+                    int hs[UU];
+#pragma unroll
+                    for (int u = 0; u < UU; ++u) key[u] = ok[u] ? e[u].r : kEmpty;
+                    hash_insert_all<UU>(tk, lt, key, hs, c.err);
+#pragma unroll
+                    for (int u = 0; u < UU; ++u)
+                        if (hs[u] >= 0) atomic_add_v(&tv[hs[u]], e[u].x);
                 });
             block_walk<kHeavyBatch>(src, emit, c.short_seg, c.huge_seg, sh);
             for (int s0 = 0; s0 < Ti; s0 += blockDim.x) {
