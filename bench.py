@@ -205,7 +205,7 @@ def run_gpu(args):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     os.environ["BENCH_GPU_INDEX"] = str(dev)
-    A = W.config2()
+    A = W.config2(scale=args.scale)
     f = flops_host(A)
     F = int(f.sum())
     st = torch.cuda.current_stream()
@@ -257,7 +257,7 @@ def run_gpu(args):
     phase_ms = {k: round(v / args.steps, 3) for k, v in stats["ms"].items() if v}
     traffic = None
     tf = os.path.join(ROOT, "profiles", "traffic_num_heavy.txt")
-    if os.path.exists(tf):
+    if os.path.exists(tf) and args.scale == 20:
         for line in open(tf):
             if line.startswith("bytes_per_full_launch"):
                 traffic = float(line.split()[1])
@@ -361,7 +361,9 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "flops_per_step": F, "nnz_c": info["nnz_c"],
+            "config": {"workload": WORKLOAD if args.scale == 20 else
+                       WORKLOAD.replace("scale 20 (1,048,576^2", f"scale {args.scale} ({1 << args.scale:,}^2"),
+                       "flops_per_step": F, "nnz_c": info["nnz_c"],
                        "nbatches": info["nbatches"], "budget": "80% of free HBM",
                        "l2": "inputs and outputs larger than L2 (no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
@@ -473,9 +475,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small-extras", action="store_true")
+    ap.add_argument("--scale", type=int, default=20,
+                    help="R-MAT scale of the timed product (profiling small cases; the "
+                         "benchmark workload is 20; other scales imply --quick --no-e2e --no-cpu)")
     ap.add_argument("--ref-flops", type=float, default=1.2e10,
                     help="multiplications in the CPU oracle sample")
     args = ap.parse_args()
+    if args.scale != 20:
+        args.quick = args.no_e2e = args.no_cpu = True
     if args.impl == "reference":
         run_reference(args)
     else:

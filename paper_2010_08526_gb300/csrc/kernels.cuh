@@ -593,6 +593,17 @@ __device__ __forceinline__ void hash_insert_all(uint32_t *keys, int log2T, const
     if (pending) atomicOr(err, kErrProbe);
 }
 
+// Exclusive prefix of the per-warp values n over the block's warps (all
+// threads call it; red holds >= nw ints). Contains one __syncthreads, and
+// red may be reused after the next one.
+__device__ __forceinline__ int warp_offset(int n, int *red, int warp, int nw, int lane) {
+    if (lane == 0) red[warp] = n;
+    __syncthreads();
+    const int v = lane < nw ? red[lane] : 0;
+    const int incl = warp_incl_scan(v);
+    return __shfl_sync(SPG_FULL, incl - v, warp & 31);
+}
+
 // Lookup only; -1 when absent.
 __device__ __forceinline__ int hash_find(const uint32_t *keys, int log2T, uint32_t key) {
     const uint32_t mask = (1u << log2T) - 1u;
@@ -1129,7 +1140,7 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
     if (threadIdx.x == 0) sh.pos = 0;
     __syncthreads();
     const int64_t nitems = *nitems_p;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
         const HeavyItem item = items[order[it]];
         const int64_t g = item.g;
@@ -1169,32 +1180,40 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
                     flg[r] = 1;
                 });
             block_walk<kHeavyBatch>(src, emit, c.short_seg, c.huge_seg, sh);
-            for (int w0 = 0; w0 < (R >> 2); w0 += blockDim.x) {
-                const int w = w0 + threadIdx.x;
-                const uint32_t x = w < (R >> 2) ? flg4[w] : 0u;
+            // compaction in row order: warp w owns flag words [w*per, (w+1)*per)
+            // (4 rows each); it counts them, one barrier gives each warp its
+            // offset, then it writes its rows with a running base
+            const int nwf = R >> 2;
+            const int per = (nwf + nw - 1) / nw;
+            const int wlo = warp * per, whi = min(nwf, wlo + per);
+            int n = 0;
+            for (int w = wlo + lane; w < whi; w += 32) n += __popc(flg4[w]);
+            n = warp_sum(n);
+            int o = warp_offset(n, sh.red, warp, nw, lane);
+            for (int w0 = wlo; w0 < whi; w0 += 32) {
+                const int w = w0 + lane;
+                const uint32_t x = w < whi ? flg4[w] : 0u;
                 const int n1 = __popc(x);
                 const int incl = warp_incl_scan(n1);
-                const int tot = __shfl_sync(SPG_FULL, incl, 31);
-                int wb = 0;
-                if (lane == 31 && tot) wb = atomicAdd(&sh.pos, tot);
-                wb = __shfl_sync(SPG_FULL, wb, 31);
                 if (x) {
                     flg4[w] = 0u;
-                    int o = wb + incl - n1;
+                    int oo = o + incl - n1;
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         if ((x >> (8 * b)) & 1u) {
                             const int r = w * 4 + b;
-                            if (o < mycnt) {
-                                out_rows[out0 + o] = (I)(rbase + r);
-                                out_vals[out0 + o] = acc[r];
+                            if (oo < mycnt) {
+                                out_rows[out0 + oo] = (I)(rbase + r);
+                                out_vals[out0 + oo] = acc[r];
                             }
                             acc[r] = V(0);
-                            ++o;
+                            ++oo;
                         }
                     }
                 }
+                o += __shfl_sync(SPG_FULL, incl, 31);
             }
+            if (warp == nw - 1 && lane == 0) sh.pos = o;
         } else {
             // table sized to the item: the next power of two >= 2 * count
             int lt = 6;
@@ -1209,31 +1228,38 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
                 [&](const auto &e, const auto &ok) {
                     constexpr int UU = sizeof(ok) / sizeof(ok[0]);
                     uint32_t key[UU];
-                    int hs[UU];
 #pragma unroll
                     for (int u = 0; u < UU; ++u) key[u] = ok[u] ? e[u].r : kEmpty;
+                    int hs[UU];
                     hash_insert_all<UU>(tk, lt, key, hs, c.err);
 #pragma unroll
                     for (int u = 0; u < UU; ++u)
                         if (hs[u] >= 0) atomic_add_v(&tv[hs[u]], e[u].x);
                 });
             block_walk<kHeavyBatch>(src, emit, c.short_seg, c.huge_seg, sh);
-            for (int s0 = 0; s0 < Ti; s0 += blockDim.x) {
-                const int s = s0 + threadIdx.x;
-                const uint32_t key = s < Ti ? tk[s] : kEmpty;
+            // compaction: warp w owns slots [w*per, (w+1)*per); counts, one
+            // barrier for the offsets, then writes with a running base
+            const int per = (Ti + nw - 1) / nw;
+            const int slo = warp * per, shi = min(Ti, slo + per);
+            int n = 0;
+            for (int s = slo + lane; s < shi; s += 32) n += tk[s] != kEmpty;
+            n = warp_sum(n);
+            int o = warp_offset(n, sh.red, warp, nw, lane);
+            for (int s0 = slo; s0 < shi; s0 += 32) {
+                const int s = s0 + lane;
+                const uint32_t key = s < shi ? tk[s] : kEmpty;
                 const bool occ = key != kEmpty;
                 const unsigned bal = __ballot_sync(SPG_FULL, occ);
-                int wbase = 0;
-                if (lane == 0 && bal) wbase = atomicAdd(&sh.pos, __popc(bal));
-                wbase = __shfl_sync(SPG_FULL, wbase, 0);
                 if (occ) {
-                    const int o = wbase + __popc(bal & ((1u << lane) - 1u));
-                    if (o < mycnt) {
-                        out_rows[out0 + o] = (I)key;
-                        out_vals[out0 + o] = tv[s];
+                    const int oo = o + __popc(bal & ((1u << lane) - 1u));
+                    if (oo < mycnt) {
+                        out_rows[out0 + oo] = (I)key;
+                        out_vals[out0 + oo] = tv[s];
                     }
                 }
+                o += __popc(bal);
             }
+            if (warp == nw - 1 && lane == 0) sh.pos = o;
             __syncthreads();
             // the dense view shares this memory: zero the bytes the table used
             const int used4 = (int)((sizeof(V) + 4) * Ti / 4);
