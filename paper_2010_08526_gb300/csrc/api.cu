@@ -22,7 +22,7 @@ spgemm_status cuda_fail(cudaError_t e, const char *where) {
 size_t PlanState::workspace_bytes() const {
     const DevBuf *bufs[] = {&probs, &f, &cnt, &colptr, &tier, &list_sym, &list_num, &hist, &cursor,
                             &off_sym, &off_num, &heavy_ord, &pcnt, &err, &scan_part, &wbytes,
-                            &valid_flag, &ap_end, &ap_row, &ap_val, &stage_cnt, &stage_colptr,
+                            &valid_flag, &ap_end, &ap_row, &ap_val, &apc_off, &apc_row, &apc_val, &stage_cnt, &stage_colptr,
                             &stage_pcnt, &merge_tmp, &drows, &dvals, &parts_tab, &items, &item_cnt,
                             &item_off, &item_order};
     size_t s = 0;
@@ -33,7 +33,7 @@ size_t PlanState::workspace_bytes() const {
 void PlanState::release_all() {
     DevBuf *bufs[] = {&probs, &f, &cnt, &colptr, &tier, &list_sym, &list_num, &hist, &cursor,
                       &off_sym, &off_num, &heavy_ord, &pcnt, &err, &scan_part, &wbytes,
-                      &valid_flag, &ap_end, &ap_row, &ap_val, &stage_cnt, &stage_colptr,
+                      &valid_flag, &ap_end, &ap_row, &ap_val, &apc_off, &apc_row, &apc_val, &stage_cnt, &stage_colptr,
                       &stage_pcnt, &merge_tmp, &drows, &dvals, &parts_tab, &items, &item_cnt,
                       &item_off, &item_order};
     for (auto *b : bufs) b->release();

@@ -147,10 +147,10 @@ template <class I, class V> struct Engine : EngineBase {
         set_smem(k_num_warp<SrcParts<I, V>, 1024>, mx);
         set_smem(k_bwd_warp<I, V, 512>, mx);
         set_smem(k_bwd_warp<I, V, 1024>, mx);
-        set_smem(k_num_heavy<SrcPanelRange<I, V>, 2>, mx);
-        set_smem(k_num_heavy<SrcPartsRange<I, V>, 2>, mx);
-        set_smem(k_num_heavy<SrcPanelRange<I, V>, 3>, mx);
-        set_smem(k_num_heavy<SrcPartsRange<I, V>, 3>, mx);
+        set_smem(k_num_heavy<SrcPanelRange<I, V>, SrcColRange<I, V>, 2>, mx);
+        set_smem(k_num_heavy<SrcPartsRange<I, V>, SrcPartsRange<I, V>, 2>, mx);
+        set_smem(k_num_heavy<SrcPanelRange<I, V>, SrcColRange<I, V>, 3>, mx);
+        set_smem(k_num_heavy<SrcPartsRange<I, V>, SrcPartsRange<I, V>, 3>, mx);
         (void)sv;
         done = true;
     }
@@ -400,18 +400,19 @@ template <class I, class V> struct Engine : EngineBase {
             if constexpr (!std::is_same<RSrc, DSrc>::value) {
               if (items) {
                 // 512-thread CTAs; 3 per SM when the item memory allows it
-                // (registers are then capped at 42 per thread), else 2
+                // (registers are then capped at 40 per thread), else 2
+                using HS = typename HashSrcOf<RSrc>::type;
                 const int smem = heavy_smem(cx);
                 const int stat = (int)sizeof(BlockShared<V, 512>) + 256;
                 const int per_sm = (3 * (smem + stat) <= 227 * 1024) ? 3 : 2;
                 const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * per_sm));
                 const int td = cx.tbegin(cx.ph_dense, st);
                 if (per_sm == 3)
-                    k_num_heavy<RSrc, 3><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items_dev,
-                                                                    o.rows, o.vals);
+                    k_num_heavy<RSrc, HS, 3><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items_dev,
+                                                                        o.rows, o.vals);
                 else
-                    k_num_heavy<RSrc, 2><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items_dev,
-                                                                    o.rows, o.vals);
+                    k_num_heavy<RSrc, HS, 2><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items_dev,
+                                                                        o.rows, o.vals);
                 cx.tend(td, st);
                 cx.launched();
                 SPG_CK(cudaGetLastError());
@@ -440,6 +441,9 @@ template <class I, class V> struct Engine : EngineBase {
         a.ap_end = ps.ap_end.as<int64_t>();
         a.ap_row = ps.ap_row.as<uint16_t>();
         a.ap_val = ps.ap_val.as<V>();
+        a.apc_off = ps.apc_off.as<int32_t>();
+        a.apc_row = ps.apc_row.as<uint32_t>();
+        a.apc_val = ps.apc_val.as<V>();
         return a;
     }
 
@@ -565,8 +569,17 @@ template <class I, class V> struct Engine : EngineBase {
                                                       (const V *)ps.A.vals, ka, ps.tun.log2R,
                                                       ps.ap_end.as<unsigned long long>(),
                                                       ps.ap_row.as<uint16_t>(), ps.ap_val.as<V>());
+        // the column-grouped copy read by hash-range items
+        SPG_CK(ps.apc_off.ensure(sizeof(int32_t) * (size_t)(ka * ((int64_t)ps.P + 1))));
+        SPG_CK(ps.apc_row.ensure(sizeof(uint32_t) * (nnzA + 8)));
+        SPG_CK(ps.apc_val.ensure(sizeof(V) * (nnzA + 8)));
+        const unsigned kb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ka + 255) / 256, 1 << 20));
+        k_colpanel_offsets<<<kb, 256, 0, st>>>(ps.ap_end.as<int64_t>(), ka, ps.P, ps.apc_off.as<int32_t>());
+        k_colpanel_copy<I, V><<<dim3(kb, (unsigned)std::min(ps.P, 65535)), 256, 0, st>>>(
+            (const I *)ps.A.colptr, ps.ap_end.as<int64_t>(), ps.ap_row.as<uint16_t>(), ps.ap_val.as<V>(), ka,
+            ps.P, ps.tun.log2R, ps.apc_off.as<int32_t>(), ps.apc_row.as<uint32_t>(), ps.apc_val.as<V>());
         ps.timer.end(tp, st);
-        ps.timer.launches += 5;
+        ps.timer.launches += 7;
         SPG_CK(cudaGetLastError());
         ps.panels_built = true;
         return SPGEMM_OK;

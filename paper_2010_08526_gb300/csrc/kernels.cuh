@@ -93,6 +93,11 @@ template <class I, class V> struct GemmArgs {
     const int64_t *ap_end;   // row-panelised A: segment ends, index p*ka + c
     const uint16_t *ap_row;  // local rows
     const V *ap_val;
+    // A grouped by panel within each column (column k starts at colptr[k] -
+    // colptr[0]); apc_off[k*(P+1) + p] = entries of column k in panels < p
+    const int32_t *apc_off;
+    const uint32_t *apc_row;  // global rows
+    const V *apc_val;
 };
 
 template <class I, class V> struct PartsArgs {
@@ -1014,9 +1019,9 @@ __global__ void __launch_bounds__(512, 2) k_num_dense(typename DSrc::Args sa, Ti
 // keyed by the global row). Items of one column write consecutive, disjoint
 // ranges of the column's output, in panel order.
 // ---------------------------------------------------------------------------
-constexpr int kRangeCap = 4096;
+constexpr int kRangeCap = 8192;
 constexpr int kRangeMaxPanels = 16;
-constexpr int kRangeLog2T = 13;   // 8192 slots = 2 * kRangeCap
+constexpr int kRangeLog2T = 14;   // 16384 slots = 2 * kRangeCap
 
 struct HeavyItem {
     int32_t g;      // global column
@@ -1079,6 +1084,47 @@ template <class I, class V> struct SrcPanelRange {
     __device__ __forceinline__ V val(int64_t q, V bv) const { return mul_v(__ldg(&apv[q]), bv); }
 };
 
+// Hash-range items over the column-grouped copy of A: the entries of column
+// k in panels [p0, p1) are one contiguous run, so a B entry is one segment
+// whatever the number of panels (SrcPanelRange needs one per panel).
+template <class I, class V> struct SrcColRange {
+    using Args = GemmArgs<I, V>;
+    using Val = V;
+    using Idx = I;
+    const ProbDev<I, V> *p;
+    const int32_t *apo;
+    const uint32_t *cr;
+    const V *cv;
+    int64_t b0, nb, k0, k1, a0, P1;
+    int p0, p1;
+    __device__ __forceinline__ void open(const Args &a, const TierCommon &c, int64_t g, int pp0,
+                                         int pp1, int) {
+        p = a.probs;
+        const int64_t bc = g - p->gcol0;
+        b0 = (int64_t)p->bp[bc];
+        nb = (int64_t)p->bp[bc + 1] - b0;
+        k0 = a.k0; k1 = a.k1;
+        a0 = (int64_t)p->ap[0];
+        P1 = (int64_t)c.P + 1;
+        p0 = pp0; p1 = pp1;
+        apo = a.apc_off; cr = a.apc_row; cv = a.apc_val;
+    }
+    __device__ __forceinline__ int64_t nseg() const { return nb; }
+    __device__ __forceinline__ void seg(int64_t e, int64_t &beg, int &len, V &bv, int64_t &tag) const {
+        const int64_t pe = b0 + e;
+        const int64_t k = (int64_t)__ldg(&p->bi[pe]);
+        if (k < k0 || k >= k1) { len = 0; return; }
+        const int32_t *o = apo + k * P1;
+        const int o0 = __ldg(&o[p0]), o1 = __ldg(&o[p1]);
+        beg = (int64_t)__ldg(&p->ap[k]) - a0 + o0;
+        len = o1 - o0;
+        bv = __ldg(&p->bv[pe]);
+        tag = 0;
+    }
+    __device__ __forceinline__ uint32_t row(int64_t q, int64_t) const { return __ldg(&cr[q]); }
+    __device__ __forceinline__ V val(int64_t q, V bv) const { return mul_v(__ldg(&cv[q]), bv); }
+};
+
 template <class I, class V> struct SrcPartsRange {
     using Args = PartsArgs<I, V>;
     using Val = V;
@@ -1120,7 +1166,11 @@ template <class I, class V> struct SrcPartsRange {
 // windows whose gathers a warp of the heavy kernel keeps in flight
 constexpr int kHeavyBatch = 4;
 
-template <class DSrc, int MINB>
+// the source a heavy kernel uses for hash-range items, given its panel source
+template <class RSrc> struct HashSrcOf { using type = RSrc; };
+template <class I, class V> struct HashSrcOf<SrcPanelRange<I, V>> { using type = SrcColRange<I, V>; };
+
+template <class DSrc, class HSrc, int MINB>
 __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa, TierCommon c,
                                                       const HeavyItem *items, const int32_t *order,
                                                       const int64_t *nitems_p,
@@ -1167,9 +1217,9 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
             if (mycnt == 0) continue;
         }
         const int64_t out0 = c.colptr[g] - c.out_base + ioff;
-        DSrc src;
-        src.open(sa, c, g, p0, p1, h);
         if (dense) {
+            DSrc src;
+            src.open(sa, c, g, p0, p1, h);
             const int64_t rbase = (int64_t)p0 << c.log2R;
             auto emit = load_apply(
                 [&](int64_t q, V bv, int64_t tag) { return RowVal<V>{src.row(q, tag), src.val(q, bv)}; },
@@ -1223,6 +1273,8 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
             uint32_t *tk = reinterpret_cast<uint32_t *>(smem + sizeof(V) * Ti);
             for (int s = threadIdx.x; s < Ti; s += blockDim.x) { tk[s] = kEmpty; tv[s] = V(0); }
             __syncthreads();
+            HSrc src;
+            src.open(sa, c, g, p0, p1, h);
             auto emit = load_apply_all(
                 [&](int64_t q, V bv, int64_t tag) { return RowVal<V>{src.row(q, tag), src.val(q, bv)}; },
                 [&](const auto &e, const auto &ok) {
@@ -1313,6 +1365,34 @@ __global__ void k_panel_scatter(const I *ap, const I *ai, const V *av, int64_t k
             const unsigned long long pos = atomicAdd(&cursor[p * ka + col], 1ull);
             out_row[pos] = (uint16_t)(r & mask);
             out_val[pos] = av[q];
+        }
+    }
+}
+
+// The column-grouped copy of A, from the panel-major one. Offsets: one
+// thread per column writes apo[k*(P+1) + p] = entries of column k in panels
+// < p (the panel lengths are read coalesced across the threads of a panel).
+__global__ void k_colpanel_offsets(const int64_t *ape, int64_t ka, int P, int32_t *apo);
+
+// Copy: one thread per (panel, column) segment (blockIdx.y strides the
+// panels), moving it with global rows to colptr[k] - colptr[0] + offset.
+template <class I, class V>
+__global__ void k_colpanel_copy(const I *ap, const int64_t *ape, const uint16_t *apr, const V *apv,
+                                int64_t ka, int P, int log2R, const int32_t *apo, uint32_t *cr, V *cv) {
+    const int64_t a0 = (int64_t)ap[0];
+    for (int p = blockIdx.y; p < P; p += gridDim.y) {
+        const uint32_t base = (uint32_t)p << log2R;
+        for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ka;
+             k += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t idx = (int64_t)p * ka + k;
+            const int64_t s = idx ? ape[idx - 1] : 0;
+            const int64_t e = ape[idx];
+            if (s == e) continue;
+            const int64_t d0 = (int64_t)ap[k] - a0 + apo[k * ((int64_t)P + 1) + p] - s;
+            for (int64_t q = s; q < e; ++q) {
+                cr[d0 + q] = base + apr[q];
+                cv[d0 + q] = apv[q];
+            }
         }
     }
 }

@@ -136,6 +136,7 @@ struct PlanState {
     DevBuf probs, f, cnt, colptr, tier, list_sym, list_num, hist, cursor, off_sym, off_num;
     DevBuf heavy_ord, pcnt, err, scan_part, wbytes, valid_flag;
     DevBuf ap_end, ap_row, ap_val;
+    DevBuf apc_off, apc_row, apc_val;   // A grouped by panel within each column
     DevBuf stage_cnt, stage_colptr, stage_pcnt, drows, dvals, parts_tab;  // k-split
     DevBuf merge_tmp;
     DevBuf items, item_cnt, item_off, item_order;  // heavy work items (dense panels / hash ranges)

@@ -108,6 +108,23 @@ __global__ void k_heavy_items(const int32_t *list, const int32_t *list_off, cons
     if (!mode) ncount[h] = n_items;
 }
 
+// Offsets of the column-grouped copy of A (declared with its copy kernel).
+__global__ void k_colpanel_offsets(const int64_t *ape, int64_t ka, int P, int32_t *apo) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ka;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t *o = apo + k * ((int64_t)P + 1);
+        int32_t run = 0;
+#pragma unroll 4
+        for (int p = 0; p < P; ++p) {
+            const int64_t idx = (int64_t)p * ka + k;
+            const int64_t s = idx ? ape[idx - 1] : 0;
+            o[p] = run;
+            run += (int32_t)(ape[idx] - s);
+        }
+        o[P] = run;
+    }
+}
+
 // Panel-major order of the heavy items (counting sort by first panel), so
 // that the CTAs running at the same time read the same panel of A and of the
 // panel offsets from L2. mode 0: histogram; mode 1: scatter.
