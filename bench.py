@@ -197,6 +197,25 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def pinned_d2h_peak(torch, dev):
+    """GB/s of a plain device-to-pinned-host copy (4 x 1 GiB, best of 3)."""
+    GB = 1 << 30
+    src = torch.empty(4 * GB, dtype=torch.uint8, device=f"cuda:{dev}")
+    src.fill_(1)
+    host = torch.empty(GB, dtype=torch.uint8, pin_memory=True)
+    best = 0.0
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for i in range(4):
+            host.copy_(src[i * GB:(i + 1) * GB], non_blocking=True)
+        torch.cuda.synchronize()
+        best = max(best, 4 * GB / (time.perf_counter() - t) / 1e9)
+    del src, host
+    torch.cuda.empty_cache()
+    return best
+
+
 def run_gpu(args):
     import torch
     import paper_2010_08526_gb300 as spg
@@ -339,10 +358,13 @@ def run_gpu(args):
         torch.cuda.synchronize()
         edt = (time.perf_counter() - t0) / e_steps
         bi = sum(h.numel() * h.element_size() for h in hostA)
+        eplan.close()
+        # the D2H roofline: a plain pinned copy of 4 GiB from HBM, same box
+        peak_d2h = pinned_d2h_peak(torch, dev)
         e2e = {"value": world * 2 * F / edt / 1e9, "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": edt * 1e3,
-               "d2h_gbs": bo / edt / 1e9}
-        eplan.close()
+               "d2h_gbs": bo / edt / 1e9, "d2h_peak_gbs": peak_d2h,
+               "d2h_frac": (bo / edt / 1e9) / peak_d2h if peak_d2h else None}
 
     # ---- batched persistent launch vs plain per-matrix path; fwd+bwd vs plain
     extras = {}

@@ -55,6 +55,8 @@ def _lib():
                                      vp, vp, vp]
         lib.oracle_backward.argtypes = [P(_OCSC), P(_OCSC), P(_OCSC), vp, vp]
         lib.oracle_plan_batches.argtypes = [vp, i64, i64, vp]
+        lib.oracle_prune.argtypes = [P(_OCSC), ctypes.c_int, ctypes.c_double, i64, ctypes.c_int,
+                                     vp, vp, vp]
         lib.oracle_plan_batches.restype = i64
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
@@ -169,6 +171,26 @@ def merge(parts) -> CSC:
     vals = np.zeros(nnz, dtype=np.int64 if vt == 2 else np.float64)
     lib.oracle_merge(arr, len(parts), vt, 0, _ptr(colptr), _ptr(rowidx), _ptr(vals))
     return CSC(m, n, colptr, rowidx, vals)
+
+
+def prune(C: CSC, threshold: float = float("-inf"), topk: int = 0) -> CSC:
+    """Column-wise prune of a result batch (the Markov-clustering consumer the
+    column batches of Sec. III are formed for; HipMCL prunes each batch,
+    Sec. V-F): per column keep the entries with value >= threshold, then, if
+    topk > 0, only the topk largest of them (equal values: the earlier stored
+    entry wins), written in their input order. Integer values compare against
+    the smallest integer >= threshold."""
+    vt = _vtype(C.vals.dtype)
+    h = _Held(C, vt)
+    lib = _lib()
+    colptr = np.zeros(C.ncols + 1, dtype=np.int64)
+    lib.oracle_prune(ctypes.byref(h.s), vt, float(threshold), int(topk), 1, _ptr(colptr), None, None)
+    nnz = int(colptr[-1])
+    rowidx = np.zeros(nnz, dtype=np.int64)
+    vals = np.zeros(nnz, dtype=np.int64 if vt == 2 else np.float64)
+    lib.oracle_prune(ctypes.byref(h.s), vt, float(threshold), int(topk), 0, _ptr(colptr), _ptr(rowidx),
+                     _ptr(vals))
+    return CSC(C.nrows, C.ncols, colptr, rowidx, vals)
 
 
 def backward(A: CSC, B: CSC, G: CSC):

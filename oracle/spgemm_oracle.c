@@ -270,3 +270,88 @@ int64_t oracle_plan_batches(const int64_t *w, int64_t n, int64_t cap, int64_t *b
     begin[++b] = n;
     return b;
 }
+
+/*
+ * Column-wise prune of a result batch (the consumer Sec. III's batching is
+ * shaped for: Markov clustering keeps the largest entries of every column of
+ * each batch, Sec. V-F). Per column, in storage order:
+ *   1. the candidates are the entries with value >= threshold (vtype 0:
+ *      compared in float64; vtype 2: int64 compared against the smallest
+ *      int64 >= threshold);
+ *   2. if topk > 0 and more than topk candidates remain, keep the topk with
+ *      the largest values; among equal values the earlier stored entry wins;
+ *   3. the kept entries are written in their input order.
+ * cnt_only != 0: only fill colptr_out (colptr_out[0] = 0, then the prefix of
+ * kept counts). Otherwise colptr_out must already hold those offsets.
+ */
+typedef struct {
+    int64_t pos;
+    double v;
+    int64_t vi;
+} pcand;
+
+static int g_prune_int;  /* comparator mode, set before each qsort (serial) */
+
+static int cmp_cand_desc(const void *a, const void *b) {
+    const pcand *x = (const pcand *)a, *y = (const pcand *)b;
+    if (g_prune_int) {
+        if (x->vi != y->vi) return x->vi > y->vi ? -1 : 1;
+    } else {
+        if (x->v != y->v) return x->v > y->v ? -1 : 1;
+    }
+    return (x->pos > y->pos) - (x->pos < y->pos);
+}
+
+static int cmp_cand_pos(const void *a, const void *b) {
+    const pcand *x = (const pcand *)a, *y = (const pcand *)b;
+    return (x->pos > y->pos) - (x->pos < y->pos);
+}
+
+void oracle_prune(const ocsc *C, int vtype, double threshold, int64_t topk, int cnt_only,
+                  int64_t *colptr_out, int64_t *rowidx_out, void *vals_out) {
+    const double *dv = (const double *)C->vals;
+    const int64_t *iv = (const int64_t *)C->vals;
+    int64_t ithr = INT64_MIN;
+    if (vtype == 2 && threshold > -1e300) {
+        if (threshold > 9.2e18) ithr = INT64_MAX;
+        else {
+            ithr = (int64_t)threshold;               /* truncation toward zero */
+            if ((double)ithr < threshold) ++ithr;     /* smallest int64 >= threshold */
+        }
+    }
+    int64_t maxlen = 1;
+    for (int64_t j = 0; j < C->ncols; ++j)
+        if (C->colptr[j + 1] - C->colptr[j] > maxlen) maxlen = C->colptr[j + 1] - C->colptr[j];
+    pcand *cand = (pcand *)malloc(sizeof(pcand) * (size_t)maxlen);
+    g_prune_int = vtype == 2;
+    if (cnt_only) colptr_out[0] = 0;
+    for (int64_t j = 0; j < C->ncols; ++j) {
+        int64_t nc = 0;
+        for (int64_t q = C->colptr[j]; q < C->colptr[j + 1]; ++q) {
+            const int keep = vtype == 2 ? (iv[q] >= ithr) : (dv[q] >= threshold);
+            if (keep) {
+                cand[nc].pos = q;
+                cand[nc].v = vtype == 2 ? 0.0 : dv[q];
+                cand[nc].vi = vtype == 2 ? iv[q] : 0;
+                ++nc;
+            }
+        }
+        if (topk > 0 && nc > topk) {
+            qsort(cand, (size_t)nc, sizeof(pcand), cmp_cand_desc);
+            nc = topk;
+            qsort(cand, (size_t)nc, sizeof(pcand), cmp_cand_pos);
+        }
+        if (cnt_only) {
+            colptr_out[j + 1] = colptr_out[j] + nc;
+            continue;
+        }
+        const int64_t base = colptr_out[j];
+        for (int64_t t = 0; t < nc; ++t) {
+            const int64_t q = cand[t].pos;
+            rowidx_out[base + t] = C->rowidx[q];
+            if (vtype == 2) ((int64_t *)vals_out)[base + t] = iv[q];
+            else ((double *)vals_out)[base + t] = dv[q];
+        }
+    }
+    free(cand);
+}

@@ -377,3 +377,82 @@ def test_generators_shapes_and_recipes():
     assert np.all(A5.col_counts() == 16) and np.all(B5.col_counts() == 8)
     # determinism
     assert np.array_equal(W.config1(n=256).rowidx, A1.rowidx)
+
+
+# ---------------------------------------------------------------- prune
+def _col(C, j):
+    a, b = int(C.colptr[j]), int(C.colptr[j + 1])
+    return np.asarray(C.rowidx[a:b], dtype=np.int64), np.asarray(C.vals[a:b])
+
+
+@pytest.mark.parametrize("vals", ["normal", "int"])
+@pytest.mark.parametrize("topk,thr", [(0, 0.0), (3, float("-inf")), (2, -0.5), (1, 0.25), (50, 0.0)])
+def test_prune_properties(vals, topk, thr):
+    """Prune (the per-column top-k / threshold step of the batches' consumer):
+    every output column is an order-preserving subsequence of the input, all
+    kept values pass the threshold, the count is min(topk, candidates), no
+    dropped candidate beats a kept one, and among equal values at the cut the
+    earlier stored entries are the ones kept."""
+    C = rand_csc(40, 30, 0.3, 11, vals=vals)
+    P = oracle.prune(C, thr, topk)
+    int_vals = vals == "int"
+    t = np.ceil(thr) if (int_vals and np.isfinite(thr)) else thr
+    for j in range(C.ncols):
+        r, v = _col(C, j)
+        pr, pv = _col(P, j)
+        cand = np.nonzero(v >= t)[0]
+        want = len(cand) if topk <= 0 else min(topk, len(cand))
+        assert len(pr) == want
+        # subsequence, in order
+        pos = []
+        for x in pr:
+            pos.append(int(np.nonzero(r == x)[0][0]))
+        assert pos == sorted(pos)
+        assert np.array_equal(v[pos], pv)
+        assert np.all(pv >= t)
+        dropped = np.setdiff1d(cand, pos)
+        if len(pv) and len(dropped):
+            assert v[dropped].max() <= pv.min()
+            cut = pv.min()
+            kept_at_cut = [p for p in pos if v[p] == cut]
+            dropped_at_cut = [p for p in dropped if v[p] == cut]
+            if kept_at_cut and dropped_at_cut:
+                assert max(kept_at_cut) < min(dropped_at_cut)
+
+
+def test_prune_special_cases():
+    """No threshold and no limit is the identity; topk = 1 with no threshold is
+    the column argmax (first occurrence, numpy's rule); a threshold alone keeps
+    exactly the entries numpy selects; top-k maximises the kept sum."""
+    C = rand_csc(60, 25, 0.25, 5)
+    ident = oracle.prune(C, float("-inf"), 0)
+    assert np.array_equal(ident.colptr, C.colptr)
+    assert np.array_equal(ident.rowidx, C.rowidx.astype(np.int64))
+    assert np.array_equal(ident.vals, C.vals)
+    top1 = oracle.prune(C, float("-inf"), 1)
+    for j in range(C.ncols):
+        r, v = _col(C, j)
+        pr, pv = _col(top1, j)
+        if len(v):
+            assert pr[0] == r[np.argmax(v)] and pv[0] == v.max()
+        else:
+            assert len(pr) == 0
+    thr = oracle.prune(C, 0.3, 0)
+    for j in range(C.ncols):
+        r, v = _col(C, j)
+        pr, pv = _col(thr, j)
+        assert np.array_equal(pr, r[v >= 0.3]) and np.array_equal(pv, v[v >= 0.3])
+    k = 4
+    topk = oracle.prune(C, float("-inf"), k)
+    for j in range(C.ncols):
+        _, v = _col(C, j)
+        _, pv = _col(topk, j)
+        assert np.isclose(pv.sum(), np.sort(v)[::-1][:k].sum())
+
+
+def test_prune_ties_keep_earlier_entries():
+    """All-equal column: top-k keeps the first k stored entries."""
+    n = 10
+    C = CSC(20, 1, np.array([0, n], np.int64), np.arange(19, 19 - n, -1, dtype=np.int64), np.full(n, 0.5))
+    P = oracle.prune(C, float("-inf"), 3)
+    assert np.array_equal(P.rowidx, [19, 18, 17])
