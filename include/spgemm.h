@@ -112,9 +112,14 @@ typedef struct {
     int ring_depth;          /* device output buffers kept in flight by spgemm_run_batched (>= 1; 0 = 2) */
     size_t host_slot_bytes;  /* pinned host slot size for spgemm_run_batched (0 = 256 MiB) */
     int host_slots;          /* pinned host slots (>= 2; 0 = 3) */
-    int sort_output;         /* 1: sort rows inside each output column (the paper's final output);
-                                0: unsorted */
+    int sort_output;         /* 1: sort rows inside each output column (the paper keeps the final
+                                C sorted within columns, Sec. IV-D); 0: unsorted */
     const spgemm_tuning *tuning; /* NULL = defaults */
+    int prune;               /* 1: spgemm_run_batched prunes every batch on the device before its
+                                copy to the host, with spgemm_prune's rule and the two fields
+                                below (the batch consumer of Sec. III / V-F); 0: off */
+    double prune_threshold;  /* keep values >= this (-INFINITY: no threshold) */
+    int64_t prune_topk;      /* then at most this many per column (<= 0: no limit) */
 } spgemm_opts;
 
 typedef struct spgemm_plan_s spgemm_plan;
@@ -249,6 +254,29 @@ spgemm_status spgemm_merge(const spgemm_csc *parts, int nparts, spgemm_csc *out,
                            cudaStream_t stream);
 
 /*
+ * spgemm_prune -- column-wise prune of a result batch (Markov clustering keeps
+ * the largest entries of every column of each batch, Sec. III; HipMCL prunes
+ * each batch, Sec. V-F). For each column of `in`, in storage order:
+ *   1. candidates are the entries with value >= threshold (compared in the
+ *      value type against the smallest representable value >= threshold;
+ *      NaN is never a candidate; -INFINITY keeps every non-NaN entry);
+ *   2. if topk > 0 and more than topk candidates remain, the topk largest are
+ *      kept; among equal values the earlier stored entry wins (for sorted
+ *      columns: the smaller row);
+ *   3. the kept entries are written in their input order (sorted input gives
+ *      sorted output).
+ * `in`: device CSC as produced by spgemm_numeric (ptr I32 or I64, idx and
+ * value types as the product). `out`: same nrows, ncols, idx_type and
+ * val_type; out->ptr_type SPGEMM_I64. Two calls, as spgemm_merge: with
+ * out->rowidx == NULL the call fills out->colptr (device, ncols+1 int64) and
+ * sets out->nnz, synchronising the stream once; the second call (rowidx and
+ * vals allocated with out->nnz entries, colptr unchanged) fills them.
+ * Errors: SPGEMM_ERR_INVALID, SPGEMM_ERR_OOM, SPGEMM_ERR_CUDA.
+ */
+spgemm_status spgemm_prune(const spgemm_csc *in, double threshold, int64_t topk, spgemm_csc *out,
+                           cudaStream_t stream);
+
+/*
  * spgemm_merge_noalloc -- the same merge as spgemm_merge (same arguments, same
  * two-call protocol, unsorted output) for callers that may not allocate device
  * memory, e.g. code running under another framework's fixed device-memory pool
@@ -284,6 +312,10 @@ typedef int (*spgemm_sink_fn)(void *ctx, int64_t batch, int64_t col_begin, int64
  * every batch t = 0..b-1, compute C[t] on `compute` into one of ring_depth
  * device buffers, then copy it on `copy` into pinned host slots and hand it to
  * the sink, overlapping the copy of batch t with the multiply of batch t+1.
+ * With opts.sort_output the columns arrive sorted by row; with opts.prune each
+ * batch is pruned on the device (spgemm_prune's rule) before the copy, so only
+ * the kept entries cross to the host (the plan's batches then also hold the
+ * pruned copy: at most min(nnz(C(:,j)), topk) entries per column).
  * Requires spgemm_symbolic first. Returns after the last sink call.
  * Errors: SPGEMM_ERR_SINK, SPGEMM_ERR_OOM, SPGEMM_ERR_CUDA, SPGEMM_ERR_STATE.
  */

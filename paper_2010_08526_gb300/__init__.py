@@ -12,6 +12,7 @@ Main entry points
 ``Plan``                symbolic step, batch plan, numeric per batch
 ``spgemm(A, B)``        C = A*B (all batches concatenated)
 ``merge(parts)``        sort-free hash merge of partial products
+``prune(C, thr, k)``    column-wise threshold / top-k prune of a result batch
 ``run_batched(...)``    batch loop streaming C to pinned host memory
 ``SpGEMMFn``            autograd Function (masked-SpGEMM backward)
 ``Multi``               many independent products in one pass (CUDA graph)
@@ -26,6 +27,7 @@ from .core import (
     spgemm,
     merge,
     merge_noalloc,
+    prune,
     run_batched,
     backward,
     SpGEMMFn,
@@ -33,6 +35,6 @@ from .core import (
 )
 
 __all__ = [
-    "SpgemmError", "load", "Csc", "Plan", "Tuning", "spgemm", "merge", "merge_noalloc", "run_batched",
+    "SpgemmError", "load", "Csc", "Plan", "Tuning", "spgemm", "merge", "merge_noalloc", "prune", "run_batched",
     "backward", "SpGEMMFn", "Multi",
 ]

@@ -38,6 +38,7 @@ class SpgemmOpts(ctypes.Structure):
         ("budget_bytes", ctypes.c_size_t), ("kstages", ctypes.c_int), ("ring_depth", ctypes.c_int),
         ("host_slot_bytes", ctypes.c_size_t), ("host_slots", ctypes.c_int),
         ("sort_output", ctypes.c_int), ("tuning", ctypes.POINTER(SpgemmTuning)),
+        ("prune", ctypes.c_int), ("prune_threshold", ctypes.c_double), ("prune_topk", ctypes.c_int64),
     ]
 
 
@@ -85,6 +86,7 @@ SIGNATURES = {
     "spgemm_plan_stats": (ctypes.c_int, [vp, ctypes.c_int, P(SpgemmStats)]),
     "spgemm_numeric": (ctypes.c_int, [vp, i64, P(SpgemmCsc), vp]),
     "spgemm_merge": (ctypes.c_int, [P(SpgemmCsc), ctypes.c_int, P(SpgemmCsc), vp]),
+    "spgemm_prune": (ctypes.c_int, [P(SpgemmCsc), ctypes.c_double, ctypes.c_int64, P(SpgemmCsc), vp]),
     "spgemm_merge_noalloc": (ctypes.c_int, [P(SpgemmCsc), ctypes.c_int, P(SpgemmCsc), vp]),
     "spgemm_run_batched": (ctypes.c_int, [vp, SINK_FN, vp, vp, vp]),
     "spgemm_backward": (ctypes.c_int, [vp, P(SpgemmCsc), vp, vp, vp]),

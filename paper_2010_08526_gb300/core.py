@@ -100,14 +100,23 @@ class Tuning:
 
 
 def _opts(budget=None, kstages=1, tuning: Optional[Tuning] = None, ring_depth=0,
-          host_slot_bytes=0, host_slots=0):
+          host_slot_bytes=0, host_slots=0, sort_output=False, prune=None):
     o = C.SpgemmOpts()
     o.budget_bytes = int(budget or 0)
     o.kstages = int(kstages)
     o.ring_depth = int(ring_depth)
     o.host_slot_bytes = int(host_slot_bytes)
     o.host_slots = int(host_slots)
-    o.sort_output = 0
+    o.sort_output = int(bool(sort_output))
+    if prune is not None:
+        thr, topk = prune
+        o.prune = 1
+        o.prune_threshold = float(thr)
+        o.prune_topk = int(topk)
+    else:
+        o.prune = 0
+        o.prune_threshold = float("-inf")
+        o.prune_topk = 0
     keep = None
     if tuning is not None:
         keep = tuning.struct()
@@ -123,14 +132,17 @@ class Plan:
 
     def __init__(self, A: Csc, B: Csc, *, budget: Optional[int] = None, kstages: int = 1,
                  tuning: Optional[Tuning] = None, validate: bool = False, ring_depth: int = 0,
-                 host_slot_bytes: int = 0, host_slots: int = 0,
-                 stream: Optional[torch.cuda.Stream] = None):
+                 host_slot_bytes: int = 0, host_slots: int = 0, sort_output: bool = False,
+                 prune: Optional[tuple] = None, stream: Optional[torch.cuda.Stream] = None):
+        """sort_output: rows sorted inside every column of C. prune = (threshold,
+        topk): run_batched prunes each batch on the device before the copy
+        (see prune())."""
         lib = load()
         self._lib = lib
         self.A, self.B = A, B
         self._sa, self._sb = A.struct(), B.struct()
         self._opts, self._tun = _opts(budget, kstages, tuning, ring_depth, host_slot_bytes,
-                                      host_slots)
+                                      host_slots, sort_output, prune)
         h = ctypes.c_void_p()
         check(lib.spgemm_plan_create(ctypes.byref(self._sa), ctypes.byref(self._sb),
                                      ctypes.byref(self._opts), int(validate),
@@ -231,12 +243,13 @@ class Plan:
 
 def spgemm(A: Csc, B: Csc, *, budget: Optional[int] = None, kstages: int = 1,
            tuning: Optional[Tuning] = None, validate: bool = False, stream=None,
-           ptr_dtype=torch.int64) -> Csc:
+           ptr_dtype=torch.int64, sort_output: bool = False) -> Csc:
     """C = A*B as one device CSC (batches computed one after another into
-    slices of the full output). Rows inside columns are unsorted. ptr_dtype
-    torch.int32 gives a colptr of the input index type (if nnz(C) fits)."""
+    slices of the full output). Rows inside columns are unsorted unless
+    sort_output. ptr_dtype torch.int32 gives a colptr of the input index type
+    (if nnz(C) fits)."""
     plan = Plan(A, B, budget=budget, kstages=kstages, tuning=tuning, validate=validate,
-                stream=stream)
+                sort_output=sort_output, stream=stream)
     try:
         info = plan.symbolic(stream)
         nnz = int(info["nnz_c"])
@@ -283,6 +296,30 @@ def merge(parts: List[Csc], ptr_dtype=torch.int64, stream=None, _entry="spgemm_m
     if nnz == 0:
         return out
     check(fn(arr, len(parts), ctypes.byref(so2), st))
+    return out
+
+
+def prune(Cm: Csc, threshold: float = float("-inf"), topk: int = 0, stream=None) -> Csc:
+    """Column-wise prune (spgemm_prune): per column keep the entries with
+    value >= threshold, then at most topk of the largest (topk <= 0: no
+    limit; equal values: the earlier stored entry wins), in input order."""
+    lib = load()
+    colptr = torch.empty(Cm.ncols + 1, dtype=torch.int64, device=Cm.device)
+    out = Csc(Cm.nrows, Cm.ncols, colptr, Cm.rowidx[:0], Cm.vals[:0])
+    so = out.struct()
+    so.rowidx = 0
+    so.vals = 0
+    so.nnz = 0
+    sin = Cm.struct()
+    st = _stream_handle(stream)
+    check(lib.spgemm_prune(ctypes.byref(sin), float(threshold), int(topk), ctypes.byref(so), st))
+    nnz = int(so.nnz)
+    out.rowidx = torch.empty(nnz, dtype=Cm.rowidx.dtype, device=Cm.device)
+    out.vals = torch.empty(nnz, dtype=Cm.vals.dtype, device=Cm.device)
+    if nnz == 0:
+        return out
+    so2 = out.struct()
+    check(lib.spgemm_prune(ctypes.byref(sin), float(threshold), int(topk), ctypes.byref(so2), st))
     return out
 
 

@@ -1,5 +1,6 @@
 // The C ABI (include/spgemm.h): argument checks, plan lifetime, dispatch to
 // the typed engines.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -41,6 +42,11 @@ void PlanState::release_all() {
     h_small.release();
     h_stage_colptr.release();
     h_parts.release();
+    for (auto &b : ring_pcol) b.release();
+    for (auto &b : ring_prow) b.release();
+    for (auto &b : ring_pval) b.release();
+    for (auto &b : ring_hpc) b.release();
+    for (auto &w : ring_pws) w.release();
     for (auto &b : ring_col) b.release();
     for (auto &b : ring_row) b.release();
     for (auto &b : ring_val) b.release();
@@ -106,7 +112,9 @@ spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B, const
     if (B->ncols >= 0x7fffffffLL) { set_error("B.ncols must be < 2^31-1"); return SPGEMM_ERR_INVALID; }
     const int kst = opts && opts->kstages > 0 ? opts->kstages : 1;
     if (kst > 64) { set_error("kstages must be in [1, 64]"); return SPGEMM_ERR_INVALID; }
-    if (opts && opts->sort_output) { set_error("sort_output is not supported yet"); return SPGEMM_ERR_INVALID; }
+    if (opts && opts->prune && std::isnan(opts->prune_threshold)) {
+        set_error("prune_threshold is NaN"); return SPGEMM_ERR_INVALID;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -372,6 +380,20 @@ spgemm_status spgemm_plan_check(const spgemm_plan *plan, cudaStream_t stream) {
         return SPGEMM_ERR_OVERFLOW;
     }
     return SPGEMM_OK;
+}
+
+spgemm_status spgemm_prune(const spgemm_csc *in, double threshold, int64_t topk, spgemm_csc *out,
+                           cudaStream_t stream) {
+    if (!in || !out) { set_error("NULL argument"); return SPGEMM_ERR_INVALID; }
+    spgemm_status s = check_csc(in, "in", false);
+    if (s != SPGEMM_OK) return s;
+    if (std::isnan(threshold)) { set_error("threshold is NaN"); return SPGEMM_ERR_INVALID; }
+    if (!out->colptr || out->nrows != in->nrows || out->ncols != in->ncols || out->idx_type != in->idx_type ||
+        out->val_type != in->val_type || out->ptr_type != SPGEMM_I64) {
+        set_error("out does not match in (int64 colptr required)"); return SPGEMM_ERR_INVALID;
+    }
+    if (out->rowidx && out->nnz > 0 && !out->vals) { set_error("out->vals is NULL"); return SPGEMM_ERR_INVALID; }
+    return prune_dispatch(in, threshold, topk, out, stream);
 }
 
 spgemm_status spgemm_merge(const spgemm_csc *parts, int nparts, spgemm_csc *out, cudaStream_t stream) {

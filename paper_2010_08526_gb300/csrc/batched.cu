@@ -36,11 +36,15 @@ extern "C" spgemm_status spgemm_run_batched(spgemm_plan *plan, spgemm_sink_fn si
     const int64_t *hc = ps.h_colptr.as<int64_t>();
     const int64_t nb = (int64_t)ps.batches.size();
 
+    // with opts.prune every batch is pruned on the device (into a second
+    // ring) before its copy; the host reads the pruned colptr to cut pieces
+    const bool prune = ps.opts.prune != 0;
     // pieces: column ranges whose rows + values + colptr fit one host slot
-    int64_t max_nnz = 0, max_cols = 0, max_col_bytes = 0;
+    int64_t max_nnz = 0, max_cols = 0, max_col_bytes = 0, max_pnnz = 0;
     for (auto &b : ps.batches) {
         max_nnz = std::max(max_nnz, b.nnz);
         max_cols = std::max(max_cols, b.c1 - b.c0);
+        max_pnnz = std::max(max_pnnz, b.pnnz);
     }
     for (int64_t j = 0; j < ps.n; ++j)
         max_col_bytes = std::max(max_col_bytes, (hc[j + 1] - hc[j]) * (si + sv) + 16);
@@ -59,6 +63,19 @@ extern "C" spgemm_status spgemm_run_batched(spgemm_plan *plan, spgemm_sink_fn si
         for (auto ev : freed) if (ev) cudaEventDestroy(ev);
     };
     cudaError_t e = cudaSuccess;
+    if (prune) {
+        if ((int)ps.ring_pcol.size() < R) {
+            ps.ring_pcol.resize(R); ps.ring_prow.resize(R); ps.ring_pval.resize(R);
+            ps.ring_hpc.resize(R); ps.ring_pws.resize(R);
+        }
+        for (int i = 0; i < R && e == cudaSuccess; ++i) {
+            if ((e = ps.ring_pcol[i].ensure(sizeof(int64_t) * (max_cols + 1))) != cudaSuccess) break;
+            if ((e = ps.ring_prow[i].ensure((size_t)si * (max_pnnz + 1))) != cudaSuccess) break;
+            if ((e = ps.ring_pval[i].ensure((size_t)sv * (max_pnnz + 1))) != cudaSuccess) break;
+            if ((e = ps.ring_hpc[i].ensure(sizeof(int64_t) * (max_cols + 1))) != cudaSuccess) break;
+            if ((e = ps.ring_pws[i].ensure(max_cols)) != cudaSuccess) break;
+        }
+    }
     for (int i = 0; i < R && e == cudaSuccess; ++i) {
         if ((e = dcol[i].ensure(sizeof(int64_t) * (max_cols + 1))) != cudaSuccess) break;
         if ((e = drow[i].ensure((size_t)si * (max_nnz + 1))) != cudaSuccess) break;
@@ -90,6 +107,16 @@ extern "C" spgemm_status spgemm_run_batched(spgemm_plan *plan, spgemm_sink_fn si
         C.val_type = (spgemm_value_t)ps.vtype;
         spgemm_status s = ps.eng->numeric(ps, t, &C, compute);
         if (s != SPGEMM_OK) return s;
+        if (prune) {
+            const int64_t nc = b.c1 - b.c0;
+            s = ps.eng->prune_batch(ps, nc, (const int64_t *)dcol[i].p, drow[i].p, dval[i].p,
+                                    ps.ring_pcol[i].as<int64_t>(), ps.ring_prow[i].p, ps.ring_pval[i].p,
+                                    ps.ring_pws[i], compute);
+            if (s != SPGEMM_OK) return s;
+            cudaError_t ce = cudaMemcpyAsync(ps.ring_hpc[i].p, ps.ring_pcol[i].p, sizeof(int64_t) * (size_t)(nc + 1),
+                                             cudaMemcpyDeviceToHost, compute);
+            if (ce != cudaSuccess) return cuda_fail(ce, "pruned colptr copy");
+        }
         cudaError_t ee = cudaEventRecord(ready[i], compute);
         return ee == cudaSuccess ? SPGEMM_OK : cuda_fail(ee, "cudaEventRecord");
     };
@@ -133,12 +160,22 @@ extern "C" spgemm_status spgemm_run_batched(spgemm_plan *plan, spgemm_sink_fn si
         const int i = (int)(t % R);
         const Batch &b = ps.batches[(size_t)t];
         if ((e = cudaStreamWaitEvent(copy, ready[i], 0)) != cudaSuccess) { status = cuda_fail(e, "wait"); break; }
+        // offsets of the batch's output (pruned: read back after the prune)
+        const int64_t *pc = nullptr;
+        if (prune) {
+            if ((e = cudaEventSynchronize(ready[i])) != cudaSuccess) { status = cuda_fail(e, "prune wait"); break; }
+            pc = ps.ring_hpc[i].as<int64_t>();
+        }
+        auto off = [&](int64_t col) { return prune ? pc[col - b.c0] : hc[col] - hc[b.c0]; };
+        char *src_col = (char *)(prune ? ps.ring_pcol[i].p : dcol[i].p);
+        char *src_row = (char *)(prune ? ps.ring_prow[i].p : drow[i].p);
+        char *src_val = (char *)(prune ? ps.ring_pval[i].p : dval[i].p);
         int64_t c = b.c0;
         while (c < b.c1 && status == SPGEMM_OK) {
             // largest column range from c that fits one slot
             int64_t c1 = c + 1;
             auto bytes_of = [&](int64_t a, int64_t z) {
-                const int64_t nnz = hc[z] - hc[a];
+                const int64_t nnz = off(z) - off(a);
                 return (size_t)((z - a + 1) * 8 + 15) / 16 * 16 + (size_t)(nnz * si + 15) / 16 * 16 +
                        (size_t)(nnz * sv);
             };
@@ -155,18 +192,18 @@ extern "C" spgemm_status spgemm_run_batched(spgemm_plan *plan, spgemm_sink_fn si
                 if (status != SPGEMM_OK) break;
             }
             const int slot = (int)(piece_no % H);
-            const int64_t nnz = hc[c1] - hc[c];
-            const int64_t off = hc[c] - hc[b.c0];
+            const int64_t nnz = off(c1) - off(c);
+            const int64_t o0 = off(c);
             char *hb = (char *)hslot[slot].p;
             const size_t cp_bytes = (size_t)((c1 - c + 1) * 8 + 15) / 16 * 16;
             const size_t ri_bytes = (size_t)(nnz * si + 15) / 16 * 16;
-            e = cudaMemcpyAsync(hb, (int64_t *)dcol[i].p + (c - b.c0), (size_t)(c1 - c + 1) * 8,
+            e = cudaMemcpyAsync(hb, (int64_t *)src_col + (c - b.c0), (size_t)(c1 - c + 1) * 8,
                                 cudaMemcpyDeviceToHost, copy);
             if (e == cudaSuccess && nnz)
-                e = cudaMemcpyAsync(hb + cp_bytes, (char *)drow[i].p + off * si, (size_t)(nnz * si),
+                e = cudaMemcpyAsync(hb + cp_bytes, src_row + o0 * si, (size_t)(nnz * si),
                                     cudaMemcpyDeviceToHost, copy);
             if (e == cudaSuccess && nnz)
-                e = cudaMemcpyAsync(hb + cp_bytes + ri_bytes, (char *)dval[i].p + off * sv,
+                e = cudaMemcpyAsync(hb + cp_bytes + ri_bytes, src_val + o0 * sv,
                                     (size_t)(nnz * sv), cudaMemcpyDeviceToHost, copy);
             if (e == cudaSuccess) e = cudaEventRecord(slot_evt[slot], copy);
             if (e != cudaSuccess) { status = cuda_fail(e, "D2H copy"); break; }

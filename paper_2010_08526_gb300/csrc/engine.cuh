@@ -4,11 +4,13 @@
 
 #include <algorithm>
 #include <array>
+#include <cmath>
 #include <cstring>
 #include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
+#include "sort_prune.cuh"
 #include "plan.h"
 #include "util.h"
 
@@ -151,6 +153,9 @@ template <class I, class V> struct Engine : EngineBase {
         set_smem(k_num_heavy<SrcPartsRange<I, V>, SrcPartsRange<I, V>, 2>, mx);
         set_smem(k_num_heavy<SrcPanelRange<I, V>, SrcColRange<I, V>, 3>, mx);
         set_smem(k_num_heavy<SrcPartsRange<I, V>, SrcPartsRange<I, V>, 3>, mx);
+        set_smem(k_sort_block<I, V, 1024>, mx);
+        set_smem(k_sort_block<I, V, 8192>, mx);
+        set_smem(k_sort_items<I, V, 8192>, mx);
         (void)sv;
         done = true;
     }
@@ -635,7 +640,23 @@ template <class I, class V> struct Engine : EngineBase {
             for (int t = 0; t < ps.s; ++t) u += hs[(size_t)t * (n + 1) + j];
             return u;
         };
-        auto wprefix = [&](int64_t j) { return r * (hc[j] + unm(j)) + ptr_bytes * j; };
+        // with opts.prune a batch also holds its pruned copy (at most
+        // min(nnz_j, topk) entries per column), its colptr and the prune
+        // workspace
+        const bool prune = ps.opts.prune != 0;
+        if (prune) {
+            ps.prune_prefix.assign((size_t)n + 1, 0);
+            const int64_t k = ps.opts.prune_topk;
+            for (int64_t j = 0; j < n; ++j) {
+                const int64_t c = hc[j + 1] - hc[j];
+                ps.prune_prefix[(size_t)j + 1] = ps.prune_prefix[(size_t)j] + (k > 0 && c > k ? k : c);
+            }
+        }
+        auto wprefix = [&](int64_t j) {
+            int64_t w = r * (hc[j] + unm(j)) + ptr_bytes * j;
+            if (prune) w += r * ps.prune_prefix[(size_t)j] + (ptr_bytes + kPruneWsPerCol) * j;
+            return w;
+        };
         int64_t c = 0;
         if (n == 0) {
             Batch b;
@@ -659,6 +680,7 @@ template <class I, class V> struct Engine : EngineBase {
             Batch b;
             b.c0 = c; b.c1 = lo; b.nnz = hc[lo] - hc[c];
             b.unmerged = hs ? unm(lo) - unm(c) : b.nnz;
+            b.pnnz = prune ? ps.prune_prefix[(size_t)lo] - ps.prune_prefix[(size_t)c] : b.nnz;
             ps.batches.push_back(b);
             c = lo;
         }
@@ -764,9 +786,144 @@ template <class I, class V> struct Engine : EngineBase {
                 ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
                 ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
         }
+        if (ps.opts.sort_output)
+            SPG_ST(sort_batch(cx, ps.colptr.as<int64_t>(), hc[b.c0], b.c0, b.c1, (I *)C->rowidx, (V *)C->vals,
+                              b.heavy > 0 ? ps.items.as<HeavyItem>() : nullptr,
+                              ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, st));
         SPG_CK(rebase_colptr(ps.colptr.as<int64_t>() + b.c0, b.c1 - b.c0, C->colptr,
                              C->ptr_type == SPGEMM_I64, st));
         cx.launched();
+        return SPGEMM_OK;
+    }
+
+    // ---- sorted output and prune ---------------------------------------------
+    // Sort the rows of columns [c0, c1) of a batch in place: the light columns
+    // (warp bitonic up to 32 entries, shared-memory bitonic up to 8192) and the
+    // hash-range items of the heavy columns; dense items are in row order.
+    // colptr: the plan's global offsets, base = offset of column c0.
+    static spgemm_status sort_batch(const Ctx &cx, const int64_t *colptr, int64_t base, int64_t c0,
+                                    int64_t c1, I *rows, V *vals, const HeavyItem *items,
+                                    const int64_t *nitems_dev, int64_t n_items, cudaStream_t st) {
+        const int64_t nc = c1 - c0;
+        if (nc <= 0) return SPGEMM_OK;
+        const unsigned wb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nc + 7) / 8, 1 << 20));
+        k_sort_warp<I, V><<<wb, 256, 0, st>>>(colptr, base, c0, c1, rows, vals);
+        const int cap = cx.tun.hash_cap_max;
+        const unsigned bb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nc, (int64_t)cx.nsm * 8));
+        k_sort_block<I, V, 1024><<<bb, 256, (int)(1024 * (4 + sizeof(V))), st>>>(colptr, base, c0, c1, 32,
+                                                                                 cap, rows, vals);
+        if (cap > 1024)
+            k_sort_block<I, V, 8192><<<bb, 512, (int)(8192 * (4 + sizeof(V))), st>>>(colptr, base, c0, c1,
+                                                                                   1024, cap, rows, vals);
+        if (items && n_items > 0) {
+            const unsigned ib = (unsigned)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * 2));
+            k_sort_items<I, V, 8192><<<ib, 512, (int)(8192 * (4 + sizeof(V))), st>>>(
+                items, nitems_dev, colptr, base, c0, c1, rows, vals);
+        }
+        cx.launched(items ? 4 : 3);
+        SPG_CK(cudaGetLastError());
+        return SPGEMM_OK;
+    }
+
+    // The smallest value of type V that is >= thr (so that "v >= it" in V is
+    // exactly "v >= thr" in double).
+    static V typed_threshold(double thr) {
+        if constexpr (std::is_same<V, float>::value) {
+            float t = (float)thr;
+            if (std::isfinite(thr) && (double)t < thr) t = std::nextafterf(t, INFINITY);
+            return t;
+        } else if constexpr (std::is_same<V, double>::value) {
+            return thr;
+        } else {
+            if (thr <= -9.2233720368547758e18) return INT64_MIN;
+            if (thr > 9.2233720368547748e18) return INT64_MAX;
+            return (int64_t)std::ceil(thr);
+        }
+    }
+
+    static constexpr int64_t kPruneWsPerCol = 40;   // prune workspace bytes per column (PruneWs)
+
+    // Prune step 1: kept count per column, the selections, and out_colptr =
+    // exclusive scan of the counts (ncols + 1 entries, total last).
+    static spgemm_status prune_plan(const int64_t *colptr, const V *vals, int64_t ncols, V thr, int64_t topk,
+                                    PruneWs &ws, int64_t *out_colptr, int nsm, cudaStream_t st) {
+        SPG_CK(ws.ensure(ncols));
+        SPG_CK(cudaMemsetAsync(ws.nsel.p, 0, sizeof(unsigned long long), st));
+        if (ncols > 0) {
+            const unsigned wb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ncols + 7) / 8, 1 << 20));
+            k_prune_count<V><<<wb, 256, 0, st>>>(colptr, vals, ncols, thr, topk, ws.keep.as<int64_t>(),
+                                                 ws.mode.as<int8_t>(), ws.sel.as<int64_t>(),
+                                                 ws.nsel.as<unsigned long long>());
+            k_prune_select<V><<<(unsigned)nsm * 4, 256, 0, st>>>(colptr, vals, thr, topk, ws.sel.as<int64_t>(),
+                                                               ws.nsel.as<unsigned long long>(),
+                                                               ws.key.as<uint64_t>(), ws.quota.as<int64_t>());
+        }
+        SPG_CK(exclusive_scan_i64(ws.keep.as<int64_t>(), ncols, out_colptr, ws.part.as<int64_t>(), 1, st));
+        SPG_CK(cudaGetLastError());
+        return SPGEMM_OK;
+    }
+
+    // Prune step 2: the kept entries, in input order, at out_colptr.
+    template <class IO>
+    static spgemm_status prune_fill(const int64_t *colptr, const I *rows, const V *vals, int64_t ncols, V thr,
+                                    PruneWs &ws, const int64_t *out_colptr, IO *orows, V *ovals,
+                                    cudaStream_t st) {
+        if (ncols <= 0) return SPGEMM_OK;
+        const unsigned wb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ncols + 7) / 8, 1 << 20));
+        k_prune_compact<I, V, IO><<<wb, 256, 0, st>>>(colptr, rows, vals, ncols, thr, ws.mode.as<int8_t>(),
+                                                      ws.key.as<uint64_t>(), ws.quota.as<int64_t>(),
+                                                      out_colptr, orows, ovals);
+        SPG_CK(cudaGetLastError());
+        return SPGEMM_OK;
+    }
+
+    // spgemm_prune on a caller's CSC (two-call protocol).
+    static spgemm_status prune(const spgemm_csc *in, double thr_d, int64_t topk, spgemm_csc *out,
+                               cudaStream_t st) {
+        int dev = 0, nsm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t n = in->ncols;
+        const V thr = typed_threshold(thr_d);
+        DevBuf cp64;
+        const int64_t *cp = (const int64_t *)in->colptr;
+        if (in->ptr_type == SPGEMM_I32) {
+            SPG_CK(cp64.ensure(sizeof(int64_t) * (size_t)(n + 1)));
+            k_widen<int32_t><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 256) / 256, 1 << 20)), 256, 0, st>>>(
+                (const int32_t *)in->colptr, n + 1, cp64.as<int64_t>());
+            cp = cp64.as<int64_t>();
+        }
+        PruneWs ws;
+        DevBuf tmp;
+        const bool count_only = out->rowidx == nullptr;
+        int64_t *ocp = (int64_t *)out->colptr;
+        if (!count_only) {   // recount into scratch; out->colptr holds the first call's offsets
+            SPG_CK(tmp.ensure(sizeof(int64_t) * (size_t)(n + 1)));
+            ocp = tmp.as<int64_t>();
+        }
+        SPG_ST(prune_plan(cp, (const V *)in->vals, n, thr, topk, ws, ocp, nsm, st));
+        if (count_only) {
+            int64_t total = 0;
+            SPG_CK(cudaMemcpyAsync(&total, ocp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            SPG_CK(cudaStreamSynchronize(st));
+            out->nnz = total;
+            return SPGEMM_OK;
+        }
+        const int64_t *fin = (const int64_t *)out->colptr;
+        SPG_ST(prune_fill<I>(cp, (const I *)in->rowidx, (const V *)in->vals, n, thr, ws, fin, (I *)out->rowidx,
+                             (V *)out->vals, st));
+        SPG_CK(cudaStreamSynchronize(st));   // the scratch buffers go out of scope
+        return SPGEMM_OK;
+    }
+
+    spgemm_status prune_batch(PlanState &ps, int64_t ncols, const int64_t *colptr, const void *rows,
+                              const void *vals, int64_t *ocolptr, void *orows, void *ovals, PruneWs &ws,
+                              cudaStream_t st) override {
+        const V thr = typed_threshold(ps.opts.prune_threshold);
+        SPG_ST(prune_plan(colptr, (const V *)vals, ncols, thr, ps.opts.prune_topk, ws, ocolptr, ps.nsm, st));
+        SPG_ST(prune_fill<I>(colptr, (const I *)rows, (const V *)vals, ncols, thr, ws, ocolptr, (I *)orows,
+                             (V *)ovals, st));
+        ps.timer.launches += 6;
         return SPGEMM_OK;
     }
 

@@ -10,7 +10,8 @@ namespace spg {
                                          cudaStream_t);
 #define SPG_DECL2(I, V)                                                                     \
     spgemm_status merge_noalloc_##I##_##V(const spgemm_csc *, int, spgemm_csc *, cudaStream_t,   \
-                                          unsigned char *, size_t, int32_t *, int);
+                                          unsigned char *, size_t, int32_t *, int);             \
+    spgemm_status prune_##I##_##V(const spgemm_csc *, double, int64_t, spgemm_csc *, cudaStream_t);
 SPG_DECL2(i32, f64) SPG_DECL2(i32, f32) SPG_DECL2(i32, i64v)
 SPG_DECL2(i64, f64) SPG_DECL2(i64, f32) SPG_DECL2(i64, i64v)
 SPG_DECL(i32, f64) SPG_DECL(i32, f32) SPG_DECL(i32, i64v)
@@ -40,6 +41,17 @@ spgemm_status merge_dispatch(const spgemm_csc *parts, int nparts, spgemm_csc *ou
 #define MG(I, V) merge_##I##_##V(parts, nparts, out, st)
     SPG_SWITCH(idx64, vtype, MG)
 #undef MG
+    set_error("unsupported type combination");
+    return SPGEMM_ERR_INVALID;
+}
+
+spgemm_status prune_dispatch(const spgemm_csc *in, double thr, int64_t topk, spgemm_csc *out,
+                             cudaStream_t st) {
+    const int idx64 = in->idx_type == SPGEMM_I64;
+    const int vtype = in->val_type;
+#define PR(I, V) prune_##I##_##V(in, thr, topk, out, st)
+    SPG_SWITCH(idx64, vtype, PR)
+#undef PR
     set_error("unsupported type combination");
     return SPGEMM_ERR_INVALID;
 }

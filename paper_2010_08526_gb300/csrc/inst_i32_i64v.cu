@@ -14,4 +14,7 @@ spgemm_status merge_noalloc_i32_i64v(const spgemm_csc *p, int np, spgemm_csc *o,
                                      unsigned char *scratch, size_t cap, int32_t *stage, int nsm) {
     return Engine<int32_t, int64_t>::merge_noalloc(p, np, o, st, scratch, cap, stage, nsm);
 }
+spgemm_status prune_i32_i64v(const spgemm_csc *in, double thr, int64_t k, spgemm_csc *out, cudaStream_t st) {
+    return Engine<int32_t, int64_t>::prune(in, thr, k, out, st);
+}
 }  // namespace spg

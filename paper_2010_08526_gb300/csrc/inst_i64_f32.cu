@@ -14,4 +14,7 @@ spgemm_status merge_noalloc_i64_f32(const spgemm_csc *p, int np, spgemm_csc *o, 
                                      unsigned char *scratch, size_t cap, int32_t *stage, int nsm) {
     return Engine<int64_t, float>::merge_noalloc(p, np, o, st, scratch, cap, stage, nsm);
 }
+spgemm_status prune_i64_f32(const spgemm_csc *in, double thr, int64_t k, spgemm_csc *out, cudaStream_t st) {
+    return Engine<int64_t, float>::prune(in, thr, k, out, st);
+}
 }  // namespace spg

@@ -43,6 +43,26 @@ struct HostBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
+int64_t scan_partials_len(int64_t n);
+
+// Workspace of the column prune (per column: kept count, mode, selection
+// list, selected key and tie quota; scan partials).
+struct PruneWs {
+    DevBuf keep, mode, sel, nsel, key, quota, part;
+    cudaError_t ensure(int64_t ncols) {
+        cudaError_t e;
+        if ((e = keep.ensure(sizeof(int64_t) * (size_t)(ncols + 1))) != cudaSuccess) return e;
+        if ((e = mode.ensure((size_t)ncols + 16)) != cudaSuccess) return e;
+        if ((e = sel.ensure(sizeof(int64_t) * (size_t)(ncols + 1))) != cudaSuccess) return e;
+        if ((e = nsel.ensure(sizeof(unsigned long long) * 2)) != cudaSuccess) return e;
+        if ((e = key.ensure(sizeof(uint64_t) * (size_t)(ncols + 1))) != cudaSuccess) return e;
+        if ((e = quota.ensure(sizeof(int64_t) * (size_t)(ncols + 1))) != cudaSuccess) return e;
+        return part.ensure(sizeof(int64_t) * (size_t)scan_partials_len(ncols + 1));
+    }
+    size_t bytes() const { return keep.bytes + mode.bytes + sel.bytes + nsel.bytes + key.bytes + quota.bytes + part.bytes; }
+    void release() { keep.release(); mode.release(); sel.release(); nsel.release(); key.release(); quota.release(); part.release(); }
+};
+
 struct Tuning {
     int hash_cap_max = 8192;
     int log2R = 15;          // dense panel rows (set per value type at plan time)
@@ -54,6 +74,7 @@ struct Tuning {
 struct Batch {
     int64_t c0 = 0, c1 = 0;  // column range
     int64_t nnz = 0;         // nnz(C) of the batch
+    int64_t pnnz = 0;        // bound on the pruned batch (opts.prune)
     int64_t unmerged = 0;    // sum over stages of nnz(D_t) of the batch (s > 1)
     // numeric hash-tier populations: [0] the product (s = 1) or the merge,
     // [1 + t] stage t (s > 1); host copies computed from the counts
@@ -143,6 +164,10 @@ struct PlanState {
     int64_t n_items = 0;
     HostBuf h_colptr, h_small, h_stage_colptr, h_parts;
     std::vector<DevBuf> ring_col, ring_row, ring_val;   // spgemm_run_batched device ring
+    std::vector<DevBuf> ring_pcol, ring_prow, ring_pval;  // pruned copies (opts.prune)
+    std::vector<HostBuf> ring_hpc;                        // their colptrs on the host
+    std::vector<PruneWs> ring_pws;
+    std::vector<int64_t> prune_prefix;                    // sum of min(nnz_j, topk) over columns < j
     std::vector<HostBuf> host_slots;                     // spgemm_run_batched pinned slots
 
     PhaseTimer timer;
@@ -171,10 +196,19 @@ struct EngineBase {
     virtual spgemm_status numeric(PlanState &ps, int64_t t, spgemm_csc *C, cudaStream_t st) = 0;
     virtual spgemm_status backward(PlanState &ps, const spgemm_csc *G, void *dA, void *dB,
                                    cudaStream_t st) = 0;
+    // the plan's prune (opts.prune) of one batch output: colptr relative
+    // (ncols + 1, int64), into ocolptr / orows / ovals
+    virtual spgemm_status prune_batch(PlanState &ps, int64_t ncols, const int64_t *colptr, const void *rows,
+                                      const void *vals, int64_t *ocolptr, void *orows, void *ovals,
+                                      PruneWs &ws, cudaStream_t st) = 0;
 };
 
 // Type-erased standalone merge (spgemm_merge).
 spgemm_status merge_dispatch(const spgemm_csc *parts, int nparts, spgemm_csc *out,
+                             cudaStream_t st);
+
+// Type-erased column prune (spgemm_prune).
+spgemm_status prune_dispatch(const spgemm_csc *in, double threshold, int64_t topk, spgemm_csc *out,
                              cudaStream_t st);
 
 // The merge with caller-free scratch (spgemm_merge_noalloc).

@@ -1,0 +1,194 @@
+"""Sorted final output and the column-wise prune (the batch consumer: keep the
+largest entries of every column), against the oracle.
+
+* sort_output: every column of the library's C is in ascending row order and
+  equals the oracle's (sorted) product entry for entry, with no canonical
+  re-sort on our side; light columns, hash-range items and dense items of
+  heavy columns, the k-split merge and all value types.
+* spgemm_prune: bit-exact against oracle.prune applied to the same values
+  (the library's own product, copied to the host), thresholds, top-k, both,
+  ties (int64 path counts), empty columns, int32 colptr input.
+* run_batched with opts.prune: the pruned pieces streamed to the host
+  concatenate to oracle.prune of the whole sorted product.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads.csc import CSC, from_coo, shuffle_within_columns
+
+from helpers import host_csc, tol_of, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2010_08526_gb300 as spg  # noqa: E402
+
+
+def skewed(m, n, seed, hubs=3, hub_deg=None, base=4, index_dtype=np.int32, value_dtype=np.float64,
+           dist="normal"):
+    """Random columns plus a few hub rows and columns (all tiers appear)."""
+    rng = np.random.default_rng(seed)
+    hub_deg = hub_deg or max(1, m // 3)
+    rows, cols = [], []
+    counts = rng.integers(0, base * 2 + 1, n)
+    for j in range(n):
+        rows.append(rng.choice(m, size=min(m, int(counts[j])), replace=False))
+        cols.append(np.full(rows[-1].size, j))
+    for _ in range(hubs):
+        j = int(rng.integers(0, n))
+        r = rng.choice(m, size=min(m, hub_deg), replace=False)
+        rows.append(r); cols.append(np.full(r.size, j))
+        i = int(rng.integers(0, m))
+        c = rng.choice(n, size=min(n, hub_deg), replace=False)
+        rows.append(np.full(c.size, i)); cols.append(c)
+    r = np.concatenate(rows); c = np.concatenate(cols)
+    if dist == "normal":
+        v = rng.standard_normal(r.size)
+        vt = value_dtype
+    else:
+        v = np.ones(r.size, dtype=np.int64)
+        vt = np.int64
+    a = from_coo(m, n, r, c, v, dup="max", index_dtype=index_dtype, value_dtype=vt)
+    return shuffle_within_columns(a, seed + 1)
+
+
+def assert_sorted_equal(got: CSC, ref: CSC, ab=None, f=None, label=""):
+    """Rows ascending in every column and equal to the oracle's, as stored."""
+    cp = np.asarray(got.colptr, np.int64)
+    ri = np.asarray(got.rowidx, np.int64)
+    assert np.array_equal(cp, np.asarray(ref.colptr, np.int64)), f"{label}: column counts"
+    cols = np.repeat(np.arange(got.ncols), np.diff(cp))
+    inc = np.diff(ri) > 0
+    same_col = np.diff(cols) == 0
+    assert np.all(inc[same_col]), f"{label}: a column is not in ascending row order"
+    assert np.array_equal(ri, np.asarray(ref.rowidx, np.int64)), f"{label}: rows differ"
+    gv, rv = np.asarray(got.vals), np.asarray(ref.vals)
+    if np.issubdtype(gv.dtype, np.integer):
+        assert np.array_equal(gv.astype(np.int64), rv.astype(np.int64)), f"{label}: values"
+    else:
+        tol = tol_of(gv.dtype, None if f is None else np.repeat(f, np.diff(cp)))
+        err = np.abs(gv.astype(np.float64) - rv)
+        assert np.all(err <= tol * ab + 1e-300), f"{label}: max err {err.max()}"
+
+
+@pytest.mark.parametrize("case", ["light", "heavy", "heavy_f32", "ksplit", "int64"])
+def test_sort_output_matches_oracle_order(case):
+    kw = {}
+    if case == "light":
+        A = skewed(2500, 2500, 3, hubs=2, hub_deg=600, base=5)
+    elif case in ("heavy", "ksplit"):
+        A = skewed(6000, 6000, 11, hubs=4, hub_deg=2500, base=6)
+        kw["tuning"] = spg.Tuning(hash_max_cap=256, panel_rows=1024)
+        if case == "ksplit":
+            kw["kstages"] = 4
+    elif case == "heavy_f32":
+        A = skewed(5000, 5000, 21, hubs=3, hub_deg=2000, base=5, value_dtype=np.float32)
+        kw["tuning"] = spg.Tuning(hash_max_cap=512, panel_rows=2048)
+    else:
+        A = skewed(5000, 5000, 22, hubs=3, hub_deg=2000, base=5, dist="ones", index_dtype=np.int64)
+        kw["tuning"] = spg.Tuning(hash_max_cap=512, panel_rows=2048)
+    Ad = to_dev(A)
+    C = spg.spgemm(Ad, Ad, sort_output=True, **kw)
+    torch.cuda.synchronize()
+    if case in ("heavy", "ksplit"):
+        assert C.plan_info["heavy_columns"] > 0
+    ref, ab = oracle.spgemm(A, A, with_absterm=True)
+    f = oracle.flops_per_column(A, A)
+    assert_sorted_equal(host_csc(C), ref, ab, f, label=f"sorted {case}")
+
+
+def _gpu_product(A, **kw):
+    Ad = to_dev(A)
+    C = spg.spgemm(Ad, Ad, sort_output=True, **kw)
+    torch.cuda.synchronize()
+    return C
+
+
+def _same(got: CSC, ref: CSC, label):
+    assert np.array_equal(np.asarray(got.colptr, np.int64), np.asarray(ref.colptr, np.int64)), label
+    assert np.array_equal(np.asarray(got.rowidx, np.int64), np.asarray(ref.rowidx, np.int64)), label
+    gv, rv = np.asarray(got.vals), np.asarray(ref.vals)
+    if np.issubdtype(gv.dtype, np.integer):
+        assert np.array_equal(gv.astype(np.int64), rv.astype(np.int64)), label
+    else:
+        assert np.array_equal(gv.astype(np.float64), rv.astype(np.float64)), label
+
+
+@pytest.mark.parametrize("vt", [np.float64, np.float32, np.int64])
+@pytest.mark.parametrize("thr,k", [(float("-inf"), 5), (0.5, 0), (0.25, 3), (float("-inf"), 1),
+                                   (float("-inf"), 10**9), (1e30, 4)])
+def test_prune_matches_oracle_bit_exact(vt, thr, k):
+    dist = "ones" if vt == np.int64 else "normal"
+    A = skewed(3000, 3000, 5, hubs=3, hub_deg=800, base=5, value_dtype=vt, dist=dist)
+    if dist == "ones" and np.isfinite(thr) and thr < 1e20:
+        thr = 2.0 if thr > 0.3 else 1.5          # path counts are integers >= 1
+    C = _gpu_product(A, tuning=spg.Tuning(hash_max_cap=256, panel_rows=1024))
+    P = spg.prune(C, thr, k)
+    torch.cuda.synchronize()
+    ref = oracle.prune(host_csc(C), thr, k)
+    _same(host_csc(P), ref, f"prune {vt.__name__} thr={thr} k={k}")
+
+
+def test_prune_unsorted_input_and_int32_colptr():
+    """Ties go to the earlier stored entry, whatever the row order; a 32-bit
+    colptr input; empty columns."""
+    A = skewed(2000, 2000, 9, hubs=2, hub_deg=500, base=3, dist="ones")
+    Ad = to_dev(A)
+    C = spg.spgemm(Ad, Ad, ptr_dtype=torch.int32)    # unsorted
+    torch.cuda.synchronize()
+    assert C.colptr.dtype == torch.int32
+    host = host_csc(C)
+    assert np.any(np.diff(host.colptr) == 0)         # some empty columns
+    for thr, k in ((float("-inf"), 2), (2.0, 0), (1.5, 3)):
+        P = spg.prune(C, thr, k)
+        torch.cuda.synchronize()
+        _same(host_csc(P), oracle.prune(host, thr, k), f"unsorted thr={thr} k={k}")
+
+
+def test_prune_rejects_bad_arguments():
+    A = skewed(300, 300, 2, hubs=1, hub_deg=50)
+    C = _gpu_product(A)
+    with pytest.raises(spg.SpgemmError):
+        spg.prune(C, float("nan"), 3)
+
+
+@pytest.mark.parametrize("kst", [1, 3])
+def test_run_batched_prunes_before_the_copy(kst):
+    """int64 path counts: the product is exact, so the streamed selection must
+    equal the oracle's bit for bit (and ties are everywhere)."""
+    A = skewed(4000, 4000, 17, hubs=3, hub_deg=1500, base=6, dist="ones")
+    Ad = to_dev(A)
+    tun = spg.Tuning(hash_max_cap=256, panel_rows=1024)
+    full = spg.spgemm(Ad, Ad, sort_output=True, tuning=tun, kstages=kst)
+    torch.cuda.synchronize()
+    thr, k = 2.0, 7
+    ref = oracle.prune(host_csc(full), thr, k)
+    budget = A.bytes() * 3 + (1 << 20) + full.nnz * 12 // 2
+    plan = spg.Plan(Ad, Ad, budget=budget, kstages=kst, tuning=tun, sort_output=True, prune=(thr, k),
+                    host_slot_bytes=1 << 14, host_slots=2)
+    info = plan.symbolic()
+    assert info["nbatches"] >= 2
+    pieces = []
+
+    def sink(batch, c0, c1, arrs):
+        cp, ri, va = arrs
+        pieces.append((c0, c1, cp.copy(), ri.copy(), va.copy()))
+        return 0
+
+    spg.run_batched(plan, sink)
+    plan.close()
+    colptr = [0]
+    for c0, c1, cp, ri, va in pieces:
+        colptr.extend((cp[1:] + colptr[-1]).tolist())
+    got = CSC(A.nrows, A.ncols, np.array(colptr, np.int64),
+              np.concatenate([p[3] for p in pieces]).astype(np.int64),
+              np.concatenate([p[4] for p in pieces]))
+    assert pieces[0][0] == 0 and pieces[-1][1] == A.ncols
+    _same(got, ref, f"run_batched prune s={kst}")
+    assert ref.nnz < full.nnz                        # the prune did remove entries
