@@ -371,6 +371,7 @@ def run_gpu(args):
     if not args.quick:
         extras["batched_vs_plain"] = bench_multi(spg, torch, args)
         extras["fwdbwd_vs_plain"] = bench_fwdbwd(spg, torch, args)
+        extras["sorted_and_topk"] = bench_sorted_topk(spg, torch, args, A, F, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -443,6 +444,78 @@ def bench_multi(spg, torch, args):
     return {"problems": n, "flops": flops, "multi_ms": t_multi * 1e3, "plain_ms": t_plain * 1e3,
             "speedup": t_plain / t_multi, "multi_gflops": 2 * flops / t_multi / 1e9,
             "tuning": autotune.describe([(best, 0.0)])[0], "autotune_trials": autotune.describe(trials)}
+
+
+def bench_sorted_topk(spg, torch, args, A, F, dev, topk=1000):
+    """The paper's final form of C (rows sorted in every column, Sec. IV-D) on
+    the device, and the batch consumer of Sec. III / V-F end to end: every
+    batch sorted and pruned to its topk largest entries per column on the
+    device before the copy to pinned host memory."""
+    st = torch.cuda.current_stream()
+    Ad = spg.Csc.from_host(A, device=f"cuda:{dev}")
+    plan = spg.Plan(Ad, Ad, sort_output=True)
+    plan.symbolic()
+    outs = [plan.alloc_batch(t) for t in range(plan.nbatches)]
+
+    def step():
+        plan.symbolic()
+        for t in range(plan.nbatches):
+            plan.numeric(t, out=outs[t])
+    step()
+    torch.cuda.synchronize()
+    n = max(1, min(args.steps, 3))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(n):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    sms = e0.elapsed_time(e1) / n
+    plan.check_errors()
+    del outs
+    plan.close()
+    torch.cuda.empty_cache()
+
+    hostA = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (A.colptr, A.rowidx, A.vals)]
+    ebudget = 2 * (24 << 30) + 4 * A.bytes() + (4 << 30)
+    eplan = spg.Plan(Ad, Ad, budget=ebudget, host_slot_bytes=1 << 30, host_slots=4, sort_output=True,
+                     prune=(float("-inf"), topk))
+    cs = torch.cuda.Stream()
+    got = {"bytes": 0, "nnz": 0}
+
+    def sink(batch, c0, c1, arrs):
+        cp, ri, va = arrs
+        got["bytes"] += cp.nbytes + ri.nbytes + va.nbytes
+        got["nnz"] += int(va.size)
+        return 0
+
+    def estep():
+        for h, d in zip(hostA, (Ad.colptr, Ad.rowidx, Ad.vals)):
+            d.copy_(h, non_blocking=True)
+        eplan.symbolic()
+        got["bytes"] = got["nnz"] = 0
+        spg.run_batched(eplan, sink, copy=cs)
+    estep()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        estep()
+    torch.cuda.synchronize()
+    edt = (time.perf_counter() - t0) / n
+    info = eplan.query()
+    eplan.close()
+    torch.cuda.empty_cache()
+    return {
+        "sorted_device": {"value": 2 * F / (sms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": sms,
+                          "note": "symbolic + numeric with rows sorted in every column"},
+        "e2e_topk": {"value": 2 * F / edt / 1e9, "unit": UNIT, "ms_per_step": edt * 1e3, "topk": topk,
+                     "kept_nnz": got["nnz"], "d2h_bytes_per_step": got["bytes"],
+                     "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in hostA),
+                     "nbatches": info["nbatches"],
+                     "note": "each batch sorted and pruned to its top-k per column on the device, "
+                             "then streamed to pinned host memory"},
+    }
 
 
 def bench_fwdbwd(spg, torch, args):

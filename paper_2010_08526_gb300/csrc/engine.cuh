@@ -156,6 +156,7 @@ template <class I, class V> struct Engine : EngineBase {
         set_smem(k_sort_block<I, V, 1024>, mx);
         set_smem(k_sort_block<I, V, 8192>, mx);
         set_smem(k_sort_items<I, V, 8192>, mx);
+        set_smem(k_sort_items<I, V, 4096>, mx);
         (void)sv;
         done = true;
     }
@@ -816,9 +817,23 @@ template <class I, class V> struct Engine : EngineBase {
             k_sort_block<I, V, 8192><<<bb, 512, (int)(8192 * (4 + sizeof(V))), st>>>(colptr, base, c0, c1,
                                                                                    1024, cap, rows, vals);
         if (items && n_items > 0) {
-            const unsigned ib = (unsigned)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * 2));
-            k_sort_items<I, V, 8192><<<ib, 512, (int)(8192 * (4 + sizeof(V))), st>>>(
-                items, nitems_dev, colptr, base, c0, c1, rows, vals);
+            // staging for the largest hash item (range_cap rows), a bitmap
+            // over item row ranges of up to 16 panels and its 16-bit word
+            // prefix (wider ranges fall back to the bitonic sort); two CTAs
+            // per SM when that fits
+            const int64_t want = (int64_t)kRangeMaxPanels << cx.tun.log2R >> 5;
+            auto launch = [&](auto cap_tag) -> void {
+                constexpr int CAP = decltype(cap_tag)::value;
+                const int stage = (int)(CAP * (4 + sizeof(V)));
+                const int fit2 = 110 * 1024;   // bytes per CTA for two CTAs per SM
+                const int64_t room = std::max<int64_t>(fit2 - stage, 64 * 1024 - stage);
+                const int wcap = (int)std::max<int64_t>(32, std::min<int64_t>(want, room / 6));
+                const unsigned ib = (unsigned)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * 2));
+                k_sort_items<I, V, CAP><<<ib, 512, stage + 6 * wcap, st>>>(items, nitems_dev, colptr, base, c0,
+                                                                            c1, cx.tun.log2R, wcap, rows, vals);
+            };
+            if (range_cap(cx) <= 4096) launch(std::integral_constant<int, 4096>{});
+            else launch(std::integral_constant<int, 8192>{});
         }
         cx.launched(items ? 4 : 3);
         SPG_CK(cudaGetLastError());

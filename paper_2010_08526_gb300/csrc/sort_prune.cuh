@@ -109,23 +109,69 @@ __global__ void k_sort_block(const int64_t *colptr, int64_t base, int64_t c0, in
     }
 }
 
-// One CTA per hash-range item of a heavy column in [c0, c1): sorts the
-// item's segment (dense items are in row order already).
+// One CTA per hash-range item of a heavy column in [c0, c1). The item's
+// rows are distinct and lie in its row range [p0 R, p1 R), so a bitmap over
+// the range ranks them: set a bit per row, prefix the word popcounts, and an
+// entry's position is the number of set bits below its row. O(n + range/32)
+// per item. A range wider than the bitmap words given (wcap) falls back to
+// the bitonic sort. Dense items are in row order already.
 template <class I, class V, int CAP>
-__global__ void k_sort_items(const HeavyItem *items, const int64_t *nitems_p, const int64_t *colptr,
-                             int64_t base, int64_t c0, int64_t c1, I *rows, V *vals) {
+__global__ void __launch_bounds__(512, 2) k_sort_items(const HeavyItem *items, const int64_t *nitems_p, const int64_t *colptr,
+                             int64_t base, int64_t c0, int64_t c1, int log2R, int wcap, I *rows, V *vals) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t *sk = reinterpret_cast<uint32_t *>(smem);
-    V *sv = reinterpret_cast<V *>(smem + sizeof(uint32_t) * CAP);
+    uint32_t *sk = reinterpret_cast<uint32_t *>(smem);                       // CAP staged rows
+    V *sv = reinterpret_cast<V *>(smem + sizeof(uint32_t) * CAP);            // CAP staged values
+    uint32_t *bm = reinterpret_cast<uint32_t *>(smem + (sizeof(uint32_t) + sizeof(V)) * CAP);
+    uint16_t *pre = reinterpret_cast<uint16_t *>(bm + wcap);                 // word prefix (< CAP <= 2^15)
+    __shared__ uint32_t s_part[1024];
     const int64_t nitems = *nitems_p;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
         const HeavyItem item = items[it];
         if (item.cnt <= 1 || item.cnt > CAP || item.g < c0 || item.g >= c1) continue;   // dense (< 0) or trivial
         const int n = item.cnt;
         const int64_t a = colptr[item.g] - base + item.off;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) { sk[i] = (uint32_t)rows[a + i]; sv[i] = vals[a + i]; }
-        block_bitonic<CAP>(sk, sv, n);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) { rows[a + i] = (I)sk[i]; vals[a + i] = sv[i]; }
+        const int64_t r0 = (int64_t)item.p0 << log2R;
+        const int W = (int)((((int64_t)(item.p1 - item.p0)) << log2R) >> 5);
+        if (W > wcap) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) { sk[i] = (uint32_t)rows[a + i]; sv[i] = vals[a + i]; }
+            block_bitonic<CAP>(sk, sv, n);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) { rows[a + i] = (I)sk[i]; vals[a + i] = sv[i]; }
+            __syncthreads();
+            continue;
+        }
+        for (int w = threadIdx.x; w < W; w += blockDim.x) bm[w] = 0u;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t r = (uint32_t)rows[a + i];
+            sk[i] = r;
+            sv[i] = vals[a + i];
+            const uint32_t b = (uint32_t)((int64_t)r - r0);
+            atomicOr(&bm[b >> 5], 1u << (b & 31));
+        }
+        __syncthreads();
+        // exclusive prefix of the word popcounts: each thread a contiguous
+        // run of words, then a scan over the threads' sums
+        const int per = (W + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int w0 = threadIdx.x * per, w1 = min(W, w0 + per);
+        uint32_t sum = 0;
+        for (int w = w0; w < w1; ++w) sum += __popc(bm[w]);
+        s_part[threadIdx.x] = sum;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            const uint32_t t = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0u;
+            __syncthreads();
+            s_part[threadIdx.x] += t;
+            __syncthreads();
+        }
+        uint32_t run = s_part[threadIdx.x] - sum;
+        for (int w = w0; w < w1; ++w) { pre[w] = (uint16_t)run; run += __popc(bm[w]); }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t b = (uint32_t)((int64_t)sk[i] - r0);
+            const uint32_t pos = (uint32_t)pre[b >> 5] + __popc(bm[b >> 5] & ((1u << (b & 31)) - 1u));
+            rows[a + pos] = (I)sk[i];
+            vals[a + pos] = sv[i];
+        }
         __syncthreads();
     }
 }
