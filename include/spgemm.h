@@ -277,6 +277,20 @@ spgemm_status spgemm_prune(const spgemm_csc *in, double threshold, int64_t topk,
                            cudaStream_t stream);
 
 /*
+ * spgemm_transpose -- out = in^T on the device (the CSC of the transpose, i.e.
+ * the CSR of `in`). A^T serves the A A^T products of Sec. V (BELLA's shared
+ * k-mers) and the row-by-row batching Sec. IV-B mentions for square inputs:
+ * the row batches of C = A B are the column batches of C^T = B^T A^T.
+ * `out`: nrows = in.ncols, ncols = in.nrows, nnz = in.nnz, the same index and
+ * value types, colptr (in.nrows + 1 entries, I32 or I64), rowidx and vals all
+ * caller-allocated. Rows inside an output column come in unspecified order.
+ * Synchronises the stream once (the work buffers are freed on return).
+ * Errors: SPGEMM_ERR_INVALID (shapes, types, a row index outside [0, nrows)),
+ * SPGEMM_ERR_INDEX_OVERFLOW, SPGEMM_ERR_OOM, SPGEMM_ERR_CUDA.
+ */
+spgemm_status spgemm_transpose(const spgemm_csc *in, spgemm_csc *out, cudaStream_t stream);
+
+/*
  * spgemm_merge_noalloc -- the same merge as spgemm_merge (same arguments, same
  * two-call protocol, unsorted output) for callers that may not allocate device
  * memory, e.g. code running under another framework's fixed device-memory pool

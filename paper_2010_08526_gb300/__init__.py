@@ -14,6 +14,8 @@ Main entry points
 ``merge(parts)``        sort-free hash merge of partial products
 ``prune(C, thr, k)``    column-wise threshold / top-k prune of a result batch
 ``run_batched(...)``    batch loop streaming C to pinned host memory
+``transpose(A)``        A^T on the device; ``spgemm_aat(A)`` = A A^T
+``run_row_batched(..)`` row-by-row batches of C (column batches of C^T)
 ``SpGEMMFn``            autograd Function (masked-SpGEMM backward)
 ``Multi``               many independent products in one pass (CUDA graph)
 """
@@ -29,12 +31,16 @@ from .core import (
     merge_noalloc,
     prune,
     run_batched,
+    transpose,
+    spgemm_aat,
+    run_row_batched,
     backward,
     SpGEMMFn,
     Multi,
 )
 
 __all__ = [
-    "SpgemmError", "load", "Csc", "Plan", "Tuning", "spgemm", "merge", "merge_noalloc", "prune", "run_batched",
+    "SpgemmError", "load", "Csc", "Plan", "Tuning", "spgemm", "merge", "merge_noalloc", "prune", "run_batched", "transpose",
+    "spgemm_aat", "run_row_batched",
     "backward", "SpGEMMFn", "Multi",
 ]

@@ -87,6 +87,7 @@ SIGNATURES = {
     "spgemm_numeric": (ctypes.c_int, [vp, i64, P(SpgemmCsc), vp]),
     "spgemm_merge": (ctypes.c_int, [P(SpgemmCsc), ctypes.c_int, P(SpgemmCsc), vp]),
     "spgemm_prune": (ctypes.c_int, [P(SpgemmCsc), ctypes.c_double, ctypes.c_int64, P(SpgemmCsc), vp]),
+    "spgemm_transpose": (ctypes.c_int, [P(SpgemmCsc), P(SpgemmCsc), vp]),
     "spgemm_merge_noalloc": (ctypes.c_int, [P(SpgemmCsc), ctypes.c_int, P(SpgemmCsc), vp]),
     "spgemm_run_batched": (ctypes.c_int, [vp, SINK_FN, vp, vp, vp]),
     "spgemm_backward": (ctypes.c_int, [vp, P(SpgemmCsc), vp, vp, vp]),

@@ -20,7 +20,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr"]
 
 SOURCES = [
-    "api.cu", "engines.cu", "util_kernels.cu", "batched.cu", "multi.cu", "noalloc.cu",
+    "api.cu", "engines.cu", "util_kernels.cu", "batched.cu", "multi.cu", "noalloc.cu", "transpose.cu",
     "inst_i32_f64.cu", "inst_i32_f32.cu", "inst_i32_i64v.cu",
     "inst_i64_f64.cu", "inst_i64_f32.cu", "inst_i64_i64v.cu",
 ]

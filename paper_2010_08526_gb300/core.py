@@ -368,6 +368,47 @@ def run_batched(plan: Plan, sink: Callable[[int, int, int, tuple], Optional[int]
     check(st)
 
 
+def transpose(A: Csc, ptr_dtype=torch.int64, stream=None) -> Csc:
+    """A^T as a device CSC (spgemm_transpose; rows inside a column unsorted)."""
+    lib = load()
+    dev = A.device
+    out = Csc(A.ncols, A.nrows, torch.empty(A.nrows + 1, dtype=ptr_dtype, device=dev),
+              torch.empty(A.nnz, dtype=A.rowidx.dtype, device=dev),
+              torch.empty(A.nnz, dtype=A.vals.dtype, device=dev))
+    si, so = A.struct(), out.struct()
+    check(lib.spgemm_transpose(ctypes.byref(si), ctypes.byref(so), _stream_handle(stream)))
+    return out
+
+
+def spgemm_aat(A: Csc, **kw) -> Csc:
+    """C = A A^T (the BELLA overlap product of Sec. V): the transpose on the
+    device, then the column-batched product."""
+    At = transpose(A, ptr_dtype=A.colptr.dtype, stream=kw.get("stream"))
+    C = spgemm(A, At, **kw)
+    C.transposed_operand = At
+    return C
+
+
+def run_row_batched(A: Csc, B: Csc, sink: Callable[[int, int, int, tuple], Optional[int]], *,
+                    budget: Optional[int] = None, sort_output: bool = False, prune: Optional[tuple] = None,
+                    host_slot_bytes: int = 0, host_slots: int = 0, compute=None, copy=None) -> None:
+    """Row-by-row batching of C = A B (Sec. IV-B, for when nnz(A) >> nnz(B)):
+    the column batch loop on C^T = B^T A^T. sink(batch, row_begin, row_end,
+    (rowptr, colidx, vals)) receives a block of rows of C in CSR form (the
+    CSC of that column block of C^T), pinned host memory valid during the
+    call. With prune, the rule applies to the rows of C."""
+    Bt = transpose(B, ptr_dtype=B.colptr.dtype)
+    At = transpose(A, ptr_dtype=A.colptr.dtype)
+    plan = Plan(Bt, At, budget=budget, sort_output=sort_output, prune=prune,
+                host_slot_bytes=host_slot_bytes, host_slots=host_slots)
+    try:
+        plan.symbolic()
+        run_batched(plan, sink, compute=compute, copy=copy)
+    finally:
+        plan.close()
+        del Bt, At
+
+
 def backward(A: Csc, B: Csc, G: Csc, stream=None):
     """(dA, dB) for loss = sum over pattern(C) of C * G."""
     plan = Plan(A, B, stream=stream)

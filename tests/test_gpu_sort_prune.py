@@ -192,3 +192,79 @@ def test_run_batched_prunes_before_the_copy(kst):
     assert pieces[0][0] == 0 and pieces[-1][1] == A.ncols
     _same(got, ref, f"run_batched prune s={kst}")
     assert ref.nnz < full.nnz                        # the prune did remove entries
+
+
+# ------------------------------------------------------- transpose, A A^T, row batches
+from workloads.csc import transpose as host_transpose  # noqa: E402
+from helpers import assert_matches  # noqa: E402
+
+
+@pytest.mark.parametrize("it,vt,ptr", [(np.int32, np.float32, torch.int32), (np.int32, np.float64, torch.int64),
+                                       (np.int64, np.int64, torch.int64), (np.int64, np.float32, torch.int32)])
+def test_transpose_moves_every_entry(it, vt, ptr):
+    dist = "ones" if vt == np.int64 else "normal"
+    A = skewed(1700, 2300, 31, hubs=2, hub_deg=700, base=4, index_dtype=it, value_dtype=vt, dist=dist)
+    Ad = to_dev(A)
+    T = spg.transpose(Ad, ptr_dtype=ptr)
+    torch.cuda.synchronize()
+    assert (T.nrows, T.ncols, T.nnz) == (A.ncols, A.nrows, A.nnz)
+    got = oracle.canonical(host_csc(T))
+    ref = oracle.canonical(host_transpose(A))
+    assert np.array_equal(got.colptr, ref.colptr)
+    assert np.array_equal(got.rowidx, ref.rowidx)
+    assert np.array_equal(np.asarray(got.vals), np.asarray(ref.vals).astype(np.asarray(got.vals).dtype))
+    # dense check on a corner
+    d = np.zeros((A.nrows, A.ncols))
+    cols = np.repeat(np.arange(A.ncols), np.diff(A.colptr))
+    d[A.rowidx.astype(np.int64), cols] = A.vals
+    dt = np.zeros((A.ncols, A.nrows))
+    tcols = np.repeat(np.arange(got.ncols), np.diff(got.colptr))
+    dt[got.rowidx, tcols] = got.vals
+    assert np.array_equal(dt, d.T)
+
+
+def test_transpose_rejects_rows_out_of_range():
+    A = CSC(10, 3, np.array([0, 2, 3, 4], np.int32), np.array([1, 12, 4, 9], np.int32), np.ones(4))
+    Ad = to_dev(A)
+    with pytest.raises(spg.SpgemmError, match="outside"):
+        spg.transpose(Ad)
+
+
+def test_aat_matches_oracle():
+    """A A^T (Sec. V's overlap product) on a k-mer-like matrix: few nonzeros
+    per column, skewed rows."""
+    rng = np.random.default_rng(44)
+    m, n = 6000, 20000
+    r = np.minimum((rng.pareto(1.3, 2 * n) * 50).astype(np.int64), m - 1)
+    c = np.repeat(np.arange(n), 2)
+    A = from_coo(m, n, r, c, rng.random(2 * n), dup="sum", index_dtype=np.int32)
+    Ad = to_dev(A)
+    C = spg.spgemm_aat(Ad)
+    torch.cuda.synchronize()
+    At = host_transpose(A)
+    ref, ab = oracle.spgemm(A, At, with_absterm=True)
+    assert_matches(host_csc(C), ref, ab, f_col=oracle.flops_per_column(A, At), label="A A^T")
+
+
+def test_row_batched_blocks_reassemble_to_the_product():
+    A = skewed(3000, 2500, 41, hubs=2, hub_deg=900, base=5)
+    B = skewed(2500, 2800, 42, hubs=2, hub_deg=700, base=5)
+    Ad, Bd = to_dev(A), to_dev(B)
+    ref, ab = oracle.spgemm(A, B, with_absterm=True)
+    blocks = []
+
+    def sink(batch, r0, r1, arrs):
+        rp, ci, va = arrs
+        blocks.append((r0, r1, rp.copy(), ci.copy(), va.copy()))
+        return 0
+
+    budget = (A.bytes() + B.bytes()) * 4 + (1 << 20) + ref.nnz * 12 // 2
+    spg.run_row_batched(Ad, Bd, sink, budget=budget, host_slot_bytes=1 << 15, host_slots=2)
+    assert blocks[0][0] == 0 and blocks[-1][1] == A.nrows and len(blocks) >= 2
+    rowptr = [0]
+    for r0, r1, rp, ci, va in blocks:
+        rowptr.extend((rp[1:] + rowptr[-1]).tolist())
+    # the rows of C in CSR = the CSC of C^T; transpose back on the host
+    CT = CSC(B.ncols, A.nrows, np.array(rowptr, np.int64), np.concatenate([b[3] for b in blocks]).astype(np.int64),
+             np.concatenate([b[4] for b in blocks]))
+    assert_matches(host_transpose(CT), ref, ab, f_col=oracle.flops_per_column(A, B), label="row batches")
