@@ -467,6 +467,59 @@ __device__ __forceinline__ void block_walk(const Src &src, Emit &emit, int short
                     qbase = sh.qb[s_lo]; bvc = sh.bv[s_lo]; tagc = sh.tag[s_lo];
                 };
                 if constexpr (U > 0) {
+                  if (T < (1ll << 31) - 64) {
+                    // 32-bit stream positions (T fits): the same walk with
+                    // int arithmetic for the window bookkeeping
+                    const int P1 = (int)p1, TT = (int)T;
+                    int send = (int)seg_end;
+                    auto window32 = [&](int wb, int64_t &q, V &bv, int64_t &tg, bool &valid) {
+                        const int t = wb + lane;
+                        valid = t < P1;
+                        if (wb + 32 <= send) {
+                            q = qbase + t; bv = bvc; tg = tagc;
+                            if (wb + 32 == send && s_lo + 1 < nz) {
+                                ++s_lo;
+                                send = (s_lo + 1 < nz) ? (int)sh.start[s_lo + 1] : TT;
+                                qbase = sh.qb[s_lo]; bvc = sh.bv[s_lo]; tagc = sh.tag[s_lo];
+                            }
+                            return;
+                        }
+                        const int j = s_lo + 1 + lane;
+                        unsigned bit = 0u;
+                        if (j < nz) {
+                            const int d = (int)sh.start[j] - wb;
+                            if (d < 32) bit = 1u << d;
+                        }
+                        const unsigned M = __reduce_or_sync(SPG_FULL, bit);
+                        const int sg = s_lo + __popc(M & (0xffffffffu >> (31 - lane)));
+                        q = sh.qb[sg] + t;
+                        bv = sh.bv[sg]; tg = sh.tag[sg];
+                        s_lo += __popc(M);
+                        if (s_lo + 1 < nz && (int)sh.start[s_lo + 1] == wb + 32) ++s_lo;
+                        send = (s_lo + 1 < nz) ? (int)sh.start[s_lo + 1] : TT;
+                        qbase = sh.qb[s_lo]; bvc = sh.bv[s_lo]; tagc = sh.tag[s_lo];
+                    };
+                    for (int wb = (int)p0; wb < P1; wb += 32 * U) {
+                        int64_t q[U], tg[U];
+                        V b[U];
+                        bool ok[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (wb + 32 * u < P1) {
+                                window32(wb + 32 * u, q[u], b[u], tg[u], ok[u]);
+                            } else {
+                                q[u] = 0; tg[u] = 0; b[u] = V(0); ok[u] = false;
+                            }
+                        }
+                        decltype(emit.load(q[0], b[0], tg[0])) l[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            l[u] = {};
+                            if (ok[u]) l[u] = emit.load(q[u], b[u], tg[u]);
+                        }
+                        emit.apply_all(l, ok);
+                    }
+                  } else
                     for (int64_t wb = p0; wb < p1; wb += 32 * U) {
                         int64_t q[U], tg[U];
                         V b[U];
