@@ -122,17 +122,33 @@ def symbolic(A: CSC, B: CSC, krange=None, cols=None) -> np.ndarray:
     return cnt
 
 
-def spgemm(A: CSC, B: CSC, krange=None, cols=None, with_absterm: bool = False):
+def _sr_vtype(dtype, semiring: str) -> int:
+    if semiring == "plus_times":
+        return _vtype(dtype)
+    if semiring == "min_plus":
+        if _vtype(dtype) != 0:
+            raise ValueError("min_plus is defined for floating-point values")
+        return 3
+    raise ValueError(f"unknown semiring {semiring!r}")
+
+
+def spgemm(A: CSC, B: CSC, krange=None, cols=None, with_absterm: bool = False,
+           semiring: str = "plus_times"):
     """C(:, c0:c1) = A(:, K) B(K, c0:c1) by column Gustavson (Sec. II-C).
 
+    semiring "min_plus": C(i, j) = min over k of A(i, k) + B(k, j) on the same
+    structure (the algorithms hold over any semiring, Sec. II); NaN products
+    are ignored.
+
     Returns a CSC (int64 indices, float64 or int64 values, rows sorted) and,
-    if asked, the per-entry sum of |products| (the rounding-error scale).
+    if asked, the per-entry rounding-error scale: sum |products| (plus-times)
+    or the largest |a| + |b| over the entry's candidates (min-plus).
     """
     if A.ncols != B.nrows:
         raise ValueError("inner dimensions differ")
     k0, k1 = (0, A.ncols) if krange is None else krange
     c0, c1 = (0, B.ncols) if cols is None else cols
-    vt = _vtype(A.vals.dtype)
+    vt = _sr_vtype(A.vals.dtype, semiring)
     ha, hb = _Held(A, vt), _Held(B, vt)
     lib = _lib()
     cnt = np.zeros(c1 - c0, dtype=np.int64)
@@ -142,7 +158,7 @@ def spgemm(A: CSC, B: CSC, krange=None, cols=None, with_absterm: bool = False):
     nnz = int(colptr[-1])
     rowidx = np.zeros(nnz, dtype=np.int64)
     vals = np.zeros(nnz, dtype=np.int64 if vt == 2 else np.float64)
-    absterm = np.zeros(nnz, dtype=np.float64) if (with_absterm and vt == 0) else None
+    absterm = np.zeros(nnz, dtype=np.float64) if (with_absterm and vt in (0, 3)) else None
     lib.oracle_spgemm(ctypes.byref(ha.s), ctypes.byref(hb.s), vt, k0, k1, c0, c1,
                       _ptr(colptr), _ptr(rowidx), _ptr(vals),
                       _ptr(absterm) if absterm is not None else None)
@@ -150,9 +166,10 @@ def spgemm(A: CSC, B: CSC, krange=None, cols=None, with_absterm: bool = False):
     return (C, absterm) if with_absterm else C
 
 
-def merge(parts) -> CSC:
+def merge(parts, semiring: str = "plus_times") -> CSC:
     """Add entries of equal (row, col) across ``parts`` (Sec. III-A merge;
-    column j of the result formed from column j of every part, Sec. IV-D)."""
+    column j of the result formed from column j of every part, Sec. IV-D);
+    "min_plus" takes their minimum."""
     parts = list(parts)
     if not parts:
         raise ValueError("no parts")
@@ -160,7 +177,7 @@ def merge(parts) -> CSC:
     for p in parts:
         if p.nrows != m or p.ncols != n:
             raise ValueError("parts differ in shape")
-    vt = _vtype(parts[0].vals.dtype)
+    vt = _sr_vtype(parts[0].vals.dtype, semiring)
     held = [_Held(p, vt) for p in parts]
     arr = (_OCSC * len(parts))(*[h.s for h in held])
     lib = _lib()

@@ -10,7 +10,9 @@
  *   - CSC with int64 colptr / rowidx (the Python wrapper widens int32 input).
  *   - Values: vtype 0 = float64 (float32 inputs are upcast exactly by the
  *     wrapper and accumulated in float64), vtype 2 = int64 accumulated with
- *     two's-complement wrap-around (done in uint64_t).
+ *     two's-complement wrap-around (done in uint64_t), vtype 3 = float64 over
+ *     the min-plus semiring (the paper's algorithms hold over any semiring,
+ *     Sec. II): a (x) b = a + b, (+) = min, NaN products ignored (fmin).
  *   - Rows inside an input column may be in any order; (row, col) is unique.
  *   - Output columns are sorted ascending by row; numerically-zero sums are
  *     kept as structural nonzeros (a nonzero of C is any (i, j) reached by at
@@ -21,6 +23,7 @@
  * Parallelism: OpenMP over output columns with one dense accumulator per
  * thread; the arithmetic per column is the sequential definition.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -132,12 +135,18 @@ void oracle_spgemm(const ocsc *A, const ocsc *B, int vtype, int64_t k0, int64_t 
                     if (mark[i] != j) {
                         mark[i] = j;
                         rowidx_out[base + len++] = i;
-                        spa[i] = 0.0; spa_abs[i] = 0.0; spa_i[i] = 0;
+                        spa[i] = vtype == 3 ? INFINITY : 0.0;   /* the (+) identity */
+                        spa_abs[i] = 0.0; spa_i[i] = 0;
                     }
                     if (vtype == 2) {
                         uint64_t a = (uint64_t)((const int64_t *)A->vals)[q];
                         uint64_t b = (uint64_t)((const int64_t *)B->vals)[p];
                         spa_i[i] += a * b;
+                    } else if (vtype == 3) {
+                        const double a = ((const double *)A->vals)[q], b = ((const double *)B->vals)[p];
+                        spa[i] = fmin(spa[i], a + b);
+                        const double s = fabs(a) + fabs(b);
+                        if (s > spa_abs[i]) spa_abs[i] = s;
                     } else {
                         double t = ((const double *)A->vals)[q] * ((const double *)B->vals)[p];
                         spa[i] += t;
@@ -198,9 +207,11 @@ void oracle_merge(const ocsc *parts, int nparts, int vtype, int cnt_only,
                 for (int64_t q = parts[t].colptr[j]; q < parts[t].colptr[j + 1]; ++q) {
                     int64_t i = parts[t].rowidx[q];
                     if (mark[i] != j) {
-                        mark[i] = j; rowidx_out[base + len++] = i; spa[i] = 0.0; spa_i[i] = 0;
+                        mark[i] = j; rowidx_out[base + len++] = i;
+                        spa[i] = vtype == 3 ? INFINITY : 0.0; spa_i[i] = 0;
                     }
                     if (vtype == 2) spa_i[i] += (uint64_t)((const int64_t *)parts[t].vals)[q];
+                    else if (vtype == 3) spa[i] = fmin(spa[i], ((const double *)parts[t].vals)[q]);
                     else spa[i] += ((const double *)parts[t].vals)[q];
                 }
             qsort(rowidx_out + base, (size_t)len, sizeof(int64_t), cmp_i64);

@@ -456,3 +456,53 @@ def test_prune_ties_keep_earlier_entries():
     C = CSC(20, 1, np.array([0, n], np.int64), np.arange(19, 19 - n, -1, dtype=np.int64), np.full(n, 0.5))
     P = oracle.prune(C, float("-inf"), 3)
     assert np.array_equal(P.rowidx, [19, 18, 17])
+
+
+# ---------------------------------------------------------------- min-plus
+def _dense_minplus(A: CSC, B: CSC):
+    """Brute force over all k with +inf for absent entries; structure from the
+    boolean product."""
+    da = np.full((A.nrows, A.ncols), np.inf)
+    ca = np.repeat(np.arange(A.ncols), A.col_counts())
+    da[A.rowidx.astype(np.int64), ca] = A.vals
+    db = np.full((B.nrows, B.ncols), np.inf)
+    cb = np.repeat(np.arange(B.ncols), B.col_counts())
+    db[B.rowidx.astype(np.int64), cb] = B.vals
+    vals = np.min(da[:, :, None] + db[None, :, :], axis=1)
+    struct = dense_structure(A) @ dense_structure(B) > 0
+    return vals, struct
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_minplus_matches_dense_brute_force(seed):
+    """Min-plus (the paper's algorithms hold over any semiring, Sec. II):
+    C(i,j) = min_k A(i,k) + B(k,j) on the boolean product's structure."""
+    A = rand_csc(25, 18, 0.25, seed)
+    B = rand_csc(18, 21, 0.25, seed + 10)
+    C = oracle.spgemm(A, B, semiring="min_plus")
+    vals, struct = _dense_minplus(A, B)
+    assert np.array_equal(dense_structure(C) > 0, struct)
+    cc = np.repeat(np.arange(C.ncols), C.col_counts())
+    assert np.array_equal(C.vals, vals[C.rowidx, cc])
+
+
+def test_minplus_identity_and_nan_and_stages():
+    A = rand_csc(30, 30, 0.2, 7)
+    n = A.ncols
+    Z = CSC(n, n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int64), np.zeros(n))
+    C = oracle.spgemm(A, Z, semiring="min_plus")          # 0 is the (x) identity
+    ref = oracle.canonical(A)
+    assert np.array_equal(C.colptr, ref.colptr) and np.array_equal(C.rowidx, ref.rowidx)
+    assert np.array_equal(C.vals, ref.vals)
+    # a NaN product is ignored by the min
+    An = CSC(2, 2, np.array([0, 2, 2]), np.array([0, 1]), np.array([np.nan, 1.0]))
+    Bn = CSC(2, 1, np.array([0, 1]), np.array([0]), np.array([2.0]))
+    Cn = oracle.spgemm(An, Bn, semiring="min_plus")
+    assert np.array_equal(Cn.rowidx, [0, 1]) and np.isinf(Cn.vals[0]) and Cn.vals[1] == 3.0
+    # stages merged with min equal the unsplit product
+    B = rand_csc(30, 40, 0.2, 8)
+    full = oracle.spgemm(A, B, semiring="min_plus")
+    parts = [oracle.spgemm(A, B, krange=r, semiring="min_plus") for r in oracle.stage_ranges(30, 3)]
+    merged = oracle.merge(parts, semiring="min_plus")
+    assert np.array_equal(merged.colptr, full.colptr) and np.array_equal(merged.rowidx, full.rowidx)
+    assert np.array_equal(merged.vals, full.vals)
