@@ -66,6 +66,15 @@ typedef enum { SPGEMM_I32 = 0, SPGEMM_I64 = 1 } spgemm_index_t;
 typedef enum { SPGEMM_F64 = 0, SPGEMM_F32 = 1, SPGEMM_INT64 = 2 } spgemm_value_t;
 
 /*
+ * The semiring of the product (the paper's algorithms hold over any semiring,
+ * Sec. II). PLUS_TIMES: C(i,j) = sum_k A(i,k) B(k,j). MIN_PLUS (float64 and
+ * float32 values): C(i,j) = min_k A(i,k) + B(k,j), NaN sums ignored (a column
+ * entry whose every candidate is NaN holds +infinity); the structure of C is
+ * the same in both.
+ */
+typedef enum { SPGEMM_PLUS_TIMES = 0, SPGEMM_MIN_PLUS = 1 } spgemm_semiring_t;
+
+/*
  * A CSC matrix: colptr[ncols+1] (type ptr_type), rowidx[nnz] and vals[nnz]
  * (types idx_type and val_type). For inputs ptr_type must equal idx_type.
  * For outputs ptr_type may be SPGEMM_I64 while idx_type is SPGEMM_I32.
@@ -120,6 +129,9 @@ typedef struct {
                                 below (the batch consumer of Sec. III / V-F); 0: off */
     double prune_threshold;  /* keep values >= this (-INFINITY: no threshold) */
     int64_t prune_topk;      /* then at most this many per column (<= 0: no limit) */
+    int semiring;            /* spgemm_semiring_t (0 = plus-times); min-plus applies to the
+                                product, the k-stage merge and spgemm_run_batched, and
+                                spgemm_backward refuses it */
 } spgemm_opts;
 
 typedef struct spgemm_plan_s spgemm_plan;

@@ -39,6 +39,7 @@ class SpgemmOpts(ctypes.Structure):
         ("host_slot_bytes", ctypes.c_size_t), ("host_slots", ctypes.c_int),
         ("sort_output", ctypes.c_int), ("tuning", ctypes.POINTER(SpgemmTuning)),
         ("prune", ctypes.c_int), ("prune_threshold", ctypes.c_double), ("prune_topk", ctypes.c_int64),
+        ("semiring", ctypes.c_int),
     ]
 
 

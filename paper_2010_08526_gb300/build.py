@@ -23,6 +23,7 @@ SOURCES = [
     "api.cu", "engines.cu", "util_kernels.cu", "batched.cu", "multi.cu", "noalloc.cu", "transpose.cu",
     "inst_i32_f64.cu", "inst_i32_f32.cu", "inst_i32_i64v.cu",
     "inst_i64_f64.cu", "inst_i64_f32.cu", "inst_i64_i64v.cu",
+    "inst_i32_mpf32.cu", "inst_i32_mpf64.cu", "inst_i64_mpf32.cu", "inst_i64_mpf64.cu",
 ]
 
 

@@ -99,8 +99,11 @@ class Tuning:
         return t
 
 
+_SEMIRINGS = {"plus_times": 0, "min_plus": 1}
+
+
 def _opts(budget=None, kstages=1, tuning: Optional[Tuning] = None, ring_depth=0,
-          host_slot_bytes=0, host_slots=0, sort_output=False, prune=None):
+          host_slot_bytes=0, host_slots=0, sort_output=False, prune=None, semiring="plus_times"):
     o = C.SpgemmOpts()
     o.budget_bytes = int(budget or 0)
     o.kstages = int(kstages)
@@ -117,6 +120,9 @@ def _opts(budget=None, kstages=1, tuning: Optional[Tuning] = None, ring_depth=0,
         o.prune = 0
         o.prune_threshold = float("-inf")
         o.prune_topk = 0
+    if semiring not in _SEMIRINGS:
+        raise ValueError(f"unknown semiring {semiring!r}")
+    o.semiring = _SEMIRINGS[semiring]
     keep = None
     if tuning is not None:
         keep = tuning.struct()
@@ -133,16 +139,18 @@ class Plan:
     def __init__(self, A: Csc, B: Csc, *, budget: Optional[int] = None, kstages: int = 1,
                  tuning: Optional[Tuning] = None, validate: bool = False, ring_depth: int = 0,
                  host_slot_bytes: int = 0, host_slots: int = 0, sort_output: bool = False,
-                 prune: Optional[tuple] = None, stream: Optional[torch.cuda.Stream] = None):
+                 prune: Optional[tuple] = None, semiring: str = "plus_times",
+                 stream: Optional[torch.cuda.Stream] = None):
         """sort_output: rows sorted inside every column of C. prune = (threshold,
         topk): run_batched prunes each batch on the device before the copy
-        (see prune())."""
+        (see prune()). semiring: "plus_times" or "min_plus" (C(i,j) = min_k
+        A(i,k) + B(k,j), float values)."""
         lib = load()
         self._lib = lib
         self.A, self.B = A, B
         self._sa, self._sb = A.struct(), B.struct()
         self._opts, self._tun = _opts(budget, kstages, tuning, ring_depth, host_slot_bytes,
-                                      host_slots, sort_output, prune)
+                                      host_slots, sort_output, prune, semiring)
         h = ctypes.c_void_p()
         check(lib.spgemm_plan_create(ctypes.byref(self._sa), ctypes.byref(self._sb),
                                      ctypes.byref(self._opts), int(validate),
@@ -243,13 +251,13 @@ class Plan:
 
 def spgemm(A: Csc, B: Csc, *, budget: Optional[int] = None, kstages: int = 1,
            tuning: Optional[Tuning] = None, validate: bool = False, stream=None,
-           ptr_dtype=torch.int64, sort_output: bool = False) -> Csc:
+           ptr_dtype=torch.int64, sort_output: bool = False, semiring: str = "plus_times") -> Csc:
     """C = A*B as one device CSC (batches computed one after another into
     slices of the full output). Rows inside columns are unsorted unless
     sort_output. ptr_dtype torch.int32 gives a colptr of the input index type
-    (if nnz(C) fits)."""
+    (if nnz(C) fits). semiring "min_plus": C(i,j) = min_k A(i,k) + B(k,j)."""
     plan = Plan(A, B, budget=budget, kstages=kstages, tuning=tuning, validate=validate,
-                sort_output=sort_output, stream=stream)
+                sort_output=sort_output, semiring=semiring, stream=stream)
     try:
         info = plan.symbolic(stream)
         nnz = int(info["nnz_c"])

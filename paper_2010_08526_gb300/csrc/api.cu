@@ -115,6 +115,12 @@ spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B, const
     if (opts && opts->prune && std::isnan(opts->prune_threshold)) {
         set_error("prune_threshold is NaN"); return SPGEMM_ERR_INVALID;
     }
+    if (opts && opts->semiring != SPGEMM_PLUS_TIMES) {
+        if (opts->semiring != SPGEMM_MIN_PLUS) { set_error("unknown semiring"); return SPGEMM_ERR_INVALID; }
+        if (A->val_type == SPGEMM_INT64) {
+            set_error("the min-plus semiring needs floating-point values"); return SPGEMM_ERR_INVALID;
+        }
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -177,7 +183,7 @@ spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B, const
     e = cudaMemGetInfo(&freeb, &totb);
     if (e != cudaSuccess) { delete plan; return cuda_fail(e, "cudaMemGetInfo"); }
     ps.budget = (opts && opts->budget_bytes) ? opts->budget_bytes : (size_t)(0.8 * (double)freeb);
-    ps.eng = make_engine(ps.idx64, ps.vtype);
+    ps.eng = make_engine(ps.idx64, ps.vtype, opts ? opts->semiring : SPGEMM_PLUS_TIMES);
     if (!ps.eng) { set_error("unsupported type combination"); delete plan; return SPGEMM_ERR_INVALID; }
     // structural checks
     auto read_last = [&](const spgemm_csc *M, int64_t *v) -> cudaError_t {

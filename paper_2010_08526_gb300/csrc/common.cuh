@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <limits>
 #include <cuda_runtime.h>
 
 #define SPG_FULL 0xffffffffu
@@ -52,6 +53,52 @@ template <> __device__ __forceinline__ int64_t mul_v<int64_t>(int64_t a, int64_t
     return static_cast<int64_t>(static_cast<uint64_t>(a) * static_cast<uint64_t>(b));
 }
 
+// ---- min-plus semiring values ----------------------------------------------
+// The paper's algorithms hold over any semiring (Sec. II). MinPlus<F> stores
+// the plain float / double bits; the type selects the operations: a (x) b =
+// a + b, (+) = min, with NaN products ignored. Integer literals name the
+// identities, so that the kernels' V(0) (a cleared accumulator) is +infinity
+// and V(1) (the scale of a merged partial) is 0.
+template <class F> struct MinPlus {
+    F v;
+    MinPlus() = default;
+    __host__ __device__ constexpr MinPlus(int lit)
+        : v(lit == 0 ? F(__builtin_huge_val()) : (lit == 1 ? F(0) : F(lit))) {}
+    __host__ __device__ static constexpr MinPlus raw(F x) {
+        MinPlus m(1);
+        m.v = x;
+        return m;
+    }
+    __host__ __device__ friend bool operator>=(MinPlus a, MinPlus b) { return a.v >= b.v; }
+    __host__ __device__ friend bool operator==(MinPlus a, MinPlus b) { return a.v == b.v; }
+};
+template <class T> struct IsMinPlus { static constexpr bool v = false; };
+template <class F> struct IsMinPlus<MinPlus<F>> { static constexpr bool v = true; };
+
+template <> __device__ __forceinline__ MinPlus<float> mul_v<MinPlus<float>>(MinPlus<float> a, MinPlus<float> b) {
+    return MinPlus<float>::raw(a.v + b.v);
+}
+template <> __device__ __forceinline__ MinPlus<double> mul_v<MinPlus<double>>(MinPlus<double> a, MinPlus<double> b) {
+    return MinPlus<double>::raw(a.v + b.v);
+}
+// Atomic min of IEEE values through integer atomics: a non-negative value
+// orders like its bits as a signed integer, a negative one inversely to its
+// bits as an unsigned integer, so min is atomicMin on the signed view for
+// x >= 0 and atomicMax on the unsigned view for x < 0 (whatever the stored
+// value's sign). NaN is skipped.
+template <> __device__ __forceinline__ void atomic_add_v<MinPlus<float>>(MinPlus<float> *p, MinPlus<float> x) {
+    const float f = x.v;
+    if (f != f) return;
+    if (f >= 0.0f) atomicMin(reinterpret_cast<int *>(p), __float_as_int(f));
+    else atomicMax(reinterpret_cast<unsigned int *>(p), __float_as_uint(f));
+}
+template <> __device__ __forceinline__ void atomic_add_v<MinPlus<double>>(MinPlus<double> *p, MinPlus<double> x) {
+    const double f = x.v;
+    if (f != f) return;
+    if (f >= 0.0) atomicMin(reinterpret_cast<long long *>(p), __double_as_longlong(f));
+    else atomicMax(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double_as_longlong(f));
+}
+
 template <class T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(SPG_FULL, v, o);
@@ -72,3 +119,29 @@ template <class T> __device__ __forceinline__ T warp_incl_scan(T v) {
 __device__ __forceinline__ int ilog2_floor(uint64_t x) { return 63 - __clzll(x | 1); }
 
 }  // namespace spg
+
+// Loads and shuffles of min-plus values (the wrapped bits). Declared at global
+// scope, next to the built-in overloads, so that unqualified calls inside the
+// library's namespace still see those.
+__device__ __forceinline__ spg::MinPlus<float> __ldg(const spg::MinPlus<float> *p) {
+    return spg::MinPlus<float>::raw(__ldg(reinterpret_cast<const float *>(p)));
+}
+__device__ __forceinline__ spg::MinPlus<double> __ldg(const spg::MinPlus<double> *p) {
+    return spg::MinPlus<double>::raw(__ldg(reinterpret_cast<const double *>(p)));
+}
+__device__ __forceinline__ spg::MinPlus<float> __shfl_sync(unsigned mask, spg::MinPlus<float> x, int src,
+                                                           int width = 32) {
+    return spg::MinPlus<float>::raw(__shfl_sync(mask, x.v, src, width));
+}
+__device__ __forceinline__ spg::MinPlus<double> __shfl_sync(unsigned mask, spg::MinPlus<double> x, int src,
+                                                            int width = 32) {
+    return spg::MinPlus<double>::raw(__shfl_sync(mask, x.v, src, width));
+}
+__device__ __forceinline__ spg::MinPlus<float> __shfl_xor_sync(unsigned mask, spg::MinPlus<float> x, int lane_mask,
+                                                               int width = 32) {
+    return spg::MinPlus<float>::raw(__shfl_xor_sync(mask, x.v, lane_mask, width));
+}
+__device__ __forceinline__ spg::MinPlus<double> __shfl_xor_sync(unsigned mask, spg::MinPlus<double> x,
+                                                                int lane_mask, int width = 32) {
+    return spg::MinPlus<double>::raw(__shfl_xor_sync(mask, x.v, lane_mask, width));
+}

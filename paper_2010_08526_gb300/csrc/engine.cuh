@@ -843,12 +843,15 @@ template <class I, class V> struct Engine : EngineBase {
     // The smallest value of type V that is >= thr (so that "v >= it" in V is
     // exactly "v >= thr" in double).
     static V typed_threshold(double thr) {
-        if constexpr (std::is_same<V, float>::value) {
+        if constexpr (std::is_same<V, float>::value || std::is_same<V, MinPlus<float>>::value) {
             float t = (float)thr;
             if (std::isfinite(thr) && (double)t < thr) t = std::nextafterf(t, INFINITY);
-            return t;
+            if constexpr (std::is_same<V, float>::value) return t;
+            else return V::raw(t);
         } else if constexpr (std::is_same<V, double>::value) {
             return thr;
+        } else if constexpr (std::is_same<V, MinPlus<double>>::value) {
+            return V::raw(thr);
         } else {
             if (thr <= -9.2233720368547758e18) return INT64_MIN;
             if (thr > 9.2233720368547748e18) return INT64_MAX;
@@ -947,6 +950,10 @@ template <class I, class V> struct Engine : EngineBase {
                            cudaStream_t st) override {
         if (ps.vtype == SPGEMM_INT64) {
             set_error("backward needs floating-point values");
+            return SPGEMM_ERR_INVALID;
+        }
+        if (IsMinPlus<V>::v) {
+            set_error("backward is defined for the plus-times semiring only");
             return SPGEMM_ERR_INVALID;
         }
         Ctx cx = make_ctx(ps);

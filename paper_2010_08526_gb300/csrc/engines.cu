@@ -28,7 +28,17 @@ SPG_DECL(i64, f64) SPG_DECL(i64, f32) SPG_DECL(i64, i64v)
         if ((vtype) == SPGEMM_INT64) return CALL(i64, i64v);           \
     }
 
-EngineBase *make_engine(int idx64, int vtype) {
+EngineBase *make_engine_i32_mpf32();
+EngineBase *make_engine_i32_mpf64();
+EngineBase *make_engine_i64_mpf32();
+EngineBase *make_engine_i64_mpf64();
+
+EngineBase *make_engine(int idx64, int vtype, int semiring) {
+    if (semiring == SPGEMM_MIN_PLUS) {   // float values only (checked at plan time)
+        if (vtype == SPGEMM_F32) return idx64 ? make_engine_i64_mpf32() : make_engine_i32_mpf32();
+        if (vtype == SPGEMM_F64) return idx64 ? make_engine_i64_mpf64() : make_engine_i32_mpf64();
+        return nullptr;
+    }
 #define MK(I, V) make_engine_##I##_##V()
     SPG_SWITCH(idx64, vtype, MK)
 #undef MK

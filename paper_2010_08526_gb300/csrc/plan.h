@@ -219,7 +219,7 @@ spgemm_status merge_noalloc_dispatch(const spgemm_csc *parts, int nparts, spgemm
 // Argument checks shared by the merge entry points.
 spgemm_status check_merge_args(const spgemm_csc *parts, int nparts, const spgemm_csc *out);
 
-EngineBase *make_engine(int idx64, int vtype);
+EngineBase *make_engine(int idx64, int vtype, int semiring);
 
 // thread-local error message
 void set_error(const std::string &msg);
