@@ -372,6 +372,10 @@ def run_gpu(args):
         extras["batched_vs_plain"] = bench_multi(spg, torch, args)
         extras["fwdbwd_vs_plain"] = bench_fwdbwd(spg, torch, args)
         extras["sorted_and_topk"] = bench_sorted_topk(spg, torch, args, A, F, dev)
+        extras["min_plus"] = bench_step(spg, torch, args, A, dev, semiring="min_plus",
+                                        note="the same product over the min-plus semiring")
+        extras["min_plus"].pop("_counts")
+        extras["protein_2M"] = bench_protein(spg, torch, args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -444,6 +448,64 @@ def bench_multi(spg, torch, args):
     return {"problems": n, "flops": flops, "multi_ms": t_multi * 1e3, "plain_ms": t_plain * 1e3,
             "speedup": t_plain / t_multi, "multi_gflops": 2 * flops / t_multi / 1e9,
             "tuning": autotune.describe([(best, 0.0)])[0], "autotune_trials": autotune.describe(trials)}
+
+
+def bench_step(spg, torch, args, A, dev, note, **plan_kw):
+    """Device time of one symbolic + numeric step of A*A with plan options."""
+    st = torch.cuda.current_stream()
+    Ad = spg.Csc.from_host(A, device=f"cuda:{dev}")
+    plan = spg.Plan(Ad, Ad, **plan_kw)
+    plan.set_timing(True)
+    info = plan.symbolic()
+    outs = [plan.alloc_batch(t) for t in range(plan.nbatches)]
+
+    def step():
+        plan.symbolic()
+        for t in range(plan.nbatches):
+            plan.numeric(t, out=outs[t])
+    step()
+    torch.cuda.synchronize()
+    plan.stats(reset=True)
+    n = max(1, min(args.steps, 3))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(n):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    stats = plan.stats(reset=True)
+    plan.check_errors()
+    cnt = plan.column_counts().cpu().numpy()
+    del outs
+    plan.close()
+    torch.cuda.empty_cache()
+    F = int(info["flops"])
+    return {"value": 2 * F / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "flops_per_step": F,
+            "nnz_c": int(info["nnz_c"]), "nbatches": int(info["nbatches"]),
+            "phase_ms_per_step": {k: round(v / n, 3) for k, v in stats["ms"].items() if v},
+            "note": note, "_counts": cnt}
+
+
+def bench_protein(spg, torch, args, dev):
+    """The protein-similarity stand-in (2M x 2M, int64 indices, fp32, mean
+    degree 40, compression ~1): device step and the numeric phases' share of
+    the Gustavson-model bytes against the measured HBM copy peak."""
+    A = W.config3()
+    r = bench_step(spg, torch, args, A, dev, note="C = A*A, protein-similarity stand-in, 2,000,000^2, "
+                   "lognormal degrees (mean 40), int64 CSC, fp32")
+    cnt = r.pop("_counts")
+    f = flops_host(A)
+    nnzb = np.diff(A.colptr).astype(np.int64)
+    si, sv = 8, 4
+    model = float(nnzb.sum() * (si + sv + 2 * si) + f.sum() * (si + sv) + cnt.sum() * (si + sv))
+    num_ms = sum(v for k, v in r["phase_ms_per_step"].items() if k.startswith("num_"))
+    hbm, _ = peaks()
+    achieved = model / (num_ms / 1e3) / 1e9 if num_ms else 0.0
+    r["roofline_numeric"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved / hbm, "algorithmic_bytes": model, "numeric_ms": num_ms}
+    return r
 
 
 def bench_sorted_topk(spg, torch, args, A, F, dev, topk=1000):
