@@ -872,7 +872,7 @@ template <class I, class V> struct Engine : EngineBase {
             k_prune_count<V><<<wb, 256, 0, st>>>(colptr, vals, ncols, thr, topk, ws.keep.as<int64_t>(),
                                                  ws.mode.as<int8_t>(), ws.sel.as<int64_t>(),
                                                  ws.nsel.as<unsigned long long>());
-            k_prune_select<V><<<(unsigned)nsm * 4, 256, 0, st>>>(colptr, vals, thr, topk, ws.sel.as<int64_t>(),
+            k_prune_select<V><<<(unsigned)nsm * 4, 512, 0, st>>>(colptr, vals, thr, topk, ws.sel.as<int64_t>(),
                                                                ws.nsel.as<unsigned long long>(),
                                                                ws.key.as<uint64_t>(), ws.quota.as<int64_t>());
         }

@@ -217,25 +217,29 @@ __global__ void __launch_bounds__(256) k_prune_count(const int64_t *colptr, cons
 // One CTA per listed column: radix select (8 bits a pass, most significant
 // first) of the topk-th largest key among the candidates. Writes the key and
 // the quota of entries equal to it that are kept (topk minus the candidates
-// strictly above it).
+// strictly above it). Each warp counts into its own 256-bin histogram (the
+// values of a column crowd into few exponent bins, so one shared histogram
+// would serialise the atomics); the warp histograms are then summed and a
+// warp finds the digit with a suffix scan.
 template <class V>
-__global__ void __launch_bounds__(256) k_prune_select(const int64_t *colptr, const V *vals, V thr,
+__global__ void __launch_bounds__(512) k_prune_select(const int64_t *colptr, const V *vals, V thr,
                                                       int64_t topk, const int64_t *sel_list,
                                                       const unsigned long long *nsel, uint64_t *sel_key,
                                                       int64_t *sel_quota) {
-    __shared__ unsigned long long hist[256];
+    __shared__ uint32_t hist[16][256];
+    __shared__ uint32_t tot[256];
     __shared__ uint64_t s_prefix;
     __shared__ long long s_k;
     constexpr int kBits = KeyBits<V>::v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t ns = (int64_t)*nsel;
     for (int64_t s = blockIdx.x; s < ns; s += gridDim.x) {
         const int64_t j = sel_list[s];
         const int64_t a = colptr[j] - colptr[0], b = colptr[j + 1] - colptr[0];
         if (threadIdx.x == 0) { s_prefix = 0; s_k = topk; }   // want the s_k-th largest
-        __syncthreads();
         uint64_t mask = 0;   // bits of the key fixed so far
         for (int shift = kBits - 8; shift >= 0; shift -= 8) {
-            for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+            for (int i = threadIdx.x; i < 16 * 256; i += blockDim.x) (&hist[0][0])[i] = 0u;
             __syncthreads();
             const uint64_t prefix = s_prefix;
             for (int64_t q = a + threadIdx.x; q < b; q += blockDim.x) {
@@ -243,18 +247,47 @@ __global__ void __launch_bounds__(256) k_prune_select(const int64_t *colptr, con
                 if (!(v >= thr)) continue;
                 const uint64_t key = value_key(v);
                 if ((key & mask) != prefix) continue;
-                atomicAdd(&hist[(key >> shift) & 255u], 1ull);
+                atomicAdd(&hist[warp][(key >> shift) & 255u], 1u);
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                long long k = s_k;
-                int d = 255;
-                for (; d > 0; --d) {
-                    if ((long long)hist[d] >= k) break;
-                    k -= (long long)hist[d];
+            for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+                uint32_t c = 0;
+                for (int w = 0; w < nw; ++w) c += hist[w][d];
+                tot[d] = c;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                // lane l holds bins [8l, 8l+8); the digit is the highest bin
+                // at which the count from the top reaches s_k
+                const long long k = s_k;
+                uint32_t c8[8];
+                uint32_t mine = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) { c8[i] = tot[lane * 8 + i]; mine += c8[i]; }
+                // counts of the lanes above this one (bins higher than 8l+7)
+                uint32_t above = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_down_sync(SPG_FULL, above, o);
+                    if (lane + o < 32) above += t;
                 }
-                s_prefix = prefix | ((uint64_t)d << shift);
-                s_k = k;
+                above -= mine;   // exclusive suffix: bins above this lane's range
+                int dsel = -1;
+                long long kk = 0;
+                long long acc = (long long)above;
+                for (int i = 7; i >= 0; --i) {
+                    if (dsel < 0 && acc + (long long)c8[i] >= k) { dsel = lane * 8 + i; kk = k - acc; }
+                    acc += c8[i];
+                }
+                // the highest lane that found the digit wins
+                const unsigned found = __ballot_sync(SPG_FULL, dsel >= 0);
+                const int src = 31 - __clz(found);
+                const int dg = __shfl_sync(SPG_FULL, dsel, src);
+                const long long knew = __shfl_sync(SPG_FULL, kk, src);
+                if (lane == 0) {
+                    s_prefix = prefix | ((uint64_t)(dg < 0 ? 0 : dg) << shift);
+                    s_k = knew;
+                }
             }
             __syncthreads();
             mask |= (uint64_t)255 << shift;
