@@ -1366,10 +1366,15 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
             }
             if (warp == nw - 1 && lane == 0) sh.pos = o;
             __syncthreads();
-            // the dense view shares this memory: zero the bytes the table used
-            const int used4 = (int)((sizeof(V) + 4) * Ti / 4);
-            uint32_t *z = reinterpret_cast<uint32_t *>(smem);
-            for (int w = threadIdx.x; w < used4; w += blockDim.x) z[w] = 0u;
+            // the dense view shares this memory: put back the empty accumulator
+            // (V(0), the semiring's identity: +inf for min-plus) and cleared
+            // flags over the bytes the table used
+            const int64_t used = (int64_t)(sizeof(V) + 4) * Ti;
+            const int64_t nacc_all = (used + (int64_t)sizeof(V) - 1) / (int64_t)sizeof(V);
+            const int nacc = (int)(nacc_all < R ? nacc_all : R);
+            for (int r = threadIdx.x; r < nacc; r += blockDim.x) acc[r] = V(0);
+            const int64_t fl = used - (int64_t)sizeof(V) * R;   // table bytes over the flags
+            for (int r = threadIdx.x; r < fl && r < R; r += blockDim.x) flg[r] = 0;
         }
         __syncthreads();
         if (threadIdx.x == 0) {

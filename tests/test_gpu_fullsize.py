@@ -10,6 +10,9 @@ problem) at a time.
 * 512 uneven G(n,p) products (int64 ones): sampled problems bit-exact.
 * Differentiation workload (A 200k x 200k, B 200k x 100k, fp32): the whole
   forward product and both gradients against the oracle.
+* R-MAT scale 20 through the batch loop with sorted output and a top-1000
+  prune per column (sampled columns, by properties), and over the min-plus
+  semiring (sampled columns).
 """
 from __future__ import annotations
 
@@ -154,4 +157,78 @@ def test_differentiation_full_size_forward_and_gradients():
     for got, ref_g, scale in ((dA.cpu().numpy(), rA, absA), (dB.cpu().numpy(), rB, absB)):
         err = np.abs(got.astype(np.float64) - ref_g)
         assert np.all(err <= tol_of(np.float32, 17) * scale + 1e-30)
+    plan.close()
+
+
+def test_rmat_scale20_sorted_topk_stream_sampled_columns():
+    """The batch consumer at full size: every batch sorted and pruned to its
+    1000 largest entries per column on the device, streamed to the host.
+    Sampled columns against the oracle's column (float64): rows ascending, as
+    many entries as min(1000, nnz), rows a subset of the column, and the kept
+    values the column's largest within fp32 rounding (sum |terms| bound)."""
+    k = 1000
+    A = W.config2()
+    Ad = to_dev(A)
+    A = wide(A)
+    f = oracle.flops_per_column(A, A)
+    rng = np.random.default_rng(6)
+    cols = set(rng.choice(A.ncols, 10, replace=False).tolist() + np.argsort(-f)[:3].tolist())
+    plan = spg.Plan(Ad, Ad, host_slot_bytes=1 << 30, host_slots=3, sort_output=True, prune=(float("-inf"), k))
+    plan.symbolic()
+    seen = {"cols": 0, "checked": 0}
+
+    def sink(batch, c0, c1, arrs):
+        cp, ri, va = arrs
+        assert c0 == seen["cols"]
+        seen["cols"] = c1
+        for j in cols:
+            if c0 <= j < c1:
+                a, b = int(cp[j - c0]), int(cp[j - c0 + 1])
+                rows = ri[a:b].astype(np.int64)
+                vals = va[a:b].astype(np.float64)
+                ref, ab = oracle.spgemm(A, column_slice(A, j, j + 1), with_absterm=True)
+                rr, rv = ref.rowidx, ref.vals
+                assert b - a == min(k, rr.size)
+                assert np.all(np.diff(rows) > 0)
+                pos = np.searchsorted(rr, rows)
+                assert np.all(rr[np.minimum(pos, rr.size - 1)] == rows)
+                tol = tol_of(np.float32, int(f[j])) * ab[pos]
+                assert np.all(np.abs(vals - rv[pos]) <= tol + 1e-30)
+                if rr.size > k:
+                    cut = np.sort(rv)[::-1][k - 1]
+                    # kept values reach the oracle's k-th largest, up to rounding
+                    assert vals.min() >= cut - 2 * tol_of(np.float32, int(f[j])) * ab.max()
+                seen["checked"] += 1
+        return 0
+
+    spg.run_batched(plan, sink)
+    assert seen["cols"] == A.ncols and seen["checked"] == len(cols)
+    plan.close()
+
+
+def test_rmat_scale20_min_plus_sampled_columns():
+    A = W.config2()
+    Ad = to_dev(A)
+    A = wide(A)
+    plan = spg.Plan(Ad, Ad, semiring="min_plus")
+    plan.symbolic()
+    f = oracle.flops_per_column(A, A)
+    rng = np.random.default_rng(8)
+    cols = sorted(set(rng.choice(A.ncols, 12, replace=False).tolist() + np.argsort(-f)[:2].tolist()))
+    for t in range(plan.nbatches):
+        c0, c1, _ = plan.batch(t)
+        C = plan.numeric(t)
+        torch.cuda.synchronize()
+        for j in cols:
+            if c0 <= j < c1:
+                a, b = C.colptr[j - c0].item(), C.colptr[j - c0 + 1].item()
+                rows = C.rowidx[a:b].cpu().numpy().astype(np.int64)
+                vals = C.vals[a:b].cpu().numpy().astype(np.float64)
+                ref, scale = oracle.spgemm(A, column_slice(A, j, j + 1), with_absterm=True, semiring="min_plus")
+                order = np.argsort(rows)
+                assert np.array_equal(rows[order], ref.rowidx)
+                assert np.all(np.abs(vals[order] - ref.vals) <= 2 * 2.0 ** -24 * scale + 1e-30)
+        del C
+        torch.cuda.empty_cache()
+    plan.check_errors()
     plan.close()

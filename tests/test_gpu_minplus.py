@@ -125,3 +125,27 @@ def test_minplus_refusals():
     Ai = CSC(A.nrows, A.ncols, A.colptr, A.rowidx, A.vals.astype(np.int64))
     with pytest.raises(spg.SpgemmError, match="floating-point"):
         spg.Plan(to_dev(Ai), to_dev(Ai), semiring="min_plus")
+
+
+def test_minplus_dense_items_after_hash_items_on_one_cta():
+    """Many heavy columns, half with dense low panels and sparse high ones and
+    half mirrored, so that in the panel-major item order the CTAs of the heavy
+    kernel run dense items after hash-range items in the same shared memory
+    (which must come back as the min-plus identity)."""
+    rng = np.random.default_rng(12)
+    m, n = 16384, 4096
+    r = (m * rng.random(n * 60) ** 3).astype(np.int64)
+    c = np.repeat(np.arange(n), 60)
+    r = np.where(c % 2 == 1, m - 1 - r, r)
+    A = from_coo(m, n, r, c, rng.integers(0, 1000, r.size).astype(np.float64), dup="max", index_dtype=np.int32,
+                 value_dtype=np.float32)
+    rb = rng.integers(0, n, n * 12)
+    cb = np.repeat(np.arange(n), 12)
+    B = from_coo(n, n, rb, cb, rng.integers(0, 1000, rb.size).astype(np.float64), dup="max", index_dtype=np.int32,
+                 value_dtype=np.float32)
+    Ad, Bd = to_dev(A), to_dev(B)
+    C = spg.spgemm(Ad, Bd, semiring="min_plus", tuning=spg.Tuning(hash_max_cap=256, panel_rows=1024))
+    torch.cuda.synchronize()
+    assert C.plan_info["heavy_columns"] > 1000
+    ref = oracle.spgemm(A, B, semiring="min_plus")
+    compare(C, ref, exact=True, label="min-plus dense after hash")
