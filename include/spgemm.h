@@ -57,7 +57,7 @@ typedef enum {
     SPGEMM_ERR_OVERFLOW = 4,       /* a hash table probe exceeded its bound (internal error guard) */
     SPGEMM_ERR_INDEX_OVERFLOW = 5, /* an output offset does not fit the requested index type */
     SPGEMM_ERR_CUDA = 6,           /* a CUDA runtime call failed (message has the CUDA error) */
-    SPGEMM_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up */
+    SPGEMM_ERR_TIMEOUT = 7,        /* reserved: a bounded device-side wait gave up (no call waits on the device) */
     SPGEMM_ERR_SINK = 8,           /* the batch sink callback returned non-zero */
     SPGEMM_ERR_STATE = 9           /* call out of order (e.g. numeric before symbolic) */
 } spgemm_status;
