@@ -150,11 +150,19 @@ def max_over_ranks(x, world):
 
 
 # ---------------------------------------------------------------- reference arm
-def cpu_oracle_sample(A, f, target_flops):
+def cpu_oracle_sample(A, f, target_flops, threads=None):
     """Time the oracle (as it stands) on a contiguous column range of about
-    target_flops multiplications; returns (GFLOP/s, sample description, cores)."""
+    target_flops multiplications; returns (GFLOP/s, sample description, cores).
+    threads: run it on that many OpenMP threads (default: all)."""
     import oracle
     from workloads.csc import column_slice
+    if threads:
+        saved = oracle.num_threads()
+        oracle.set_threads(threads)
+        try:
+            return cpu_oracle_sample(A, f, target_flops)
+        finally:
+            oracle.set_threads(saved)
     rng = np.random.default_rng(0)
     c0 = int(rng.integers(0, A.ncols // 2))
     cs = np.cumsum(f[c0:])
@@ -380,8 +388,10 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, desc, cores, dt = cpu_oracle_sample(A, f, args.ref_flops)
+        v1, desc1, _, dt1 = cpu_oracle_sample(A, f, args.ref_flops / 16, threads=1)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
-               "seconds": dt}
+               "seconds": dt,
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": desc1, "seconds": dt1}}
 
     if rank == 0:
         line = {
