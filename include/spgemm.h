@@ -341,7 +341,10 @@ typedef int (*spgemm_sink_fn)(void *ctx, int64_t batch, int64_t col_begin, int64
  * With opts.sort_output the columns arrive sorted by row; with opts.prune each
  * batch is pruned on the device (spgemm_prune's rule) before the copy, so only
  * the kept entries cross to the host (the plan's batches then also hold the
- * pruned copy: at most min(nnz(C(:,j)), topk) entries per column).
+ * pruned copy: at most min(nnz(C(:,j)), topk) entries per column). With both,
+ * the result is that of sorting first and pruning after (equal values go to
+ * the smaller rows); for 0 < topk <= 8192 the batch is pruned unsorted and
+ * only the kept entries are sorted.
  * Requires spgemm_symbolic first. Returns after the last sink call.
  * Errors: SPGEMM_ERR_SINK, SPGEMM_ERR_OOM, SPGEMM_ERR_CUDA, SPGEMM_ERR_STATE.
  */

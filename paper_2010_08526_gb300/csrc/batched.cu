@@ -39,6 +39,13 @@ extern "C" spgemm_status spgemm_run_batched(spgemm_plan *plan, spgemm_sink_fn si
     // with opts.prune every batch is pruned on the device (into a second
     // ring) before its copy; the host reads the pruned colptr to cut pieces
     const bool prune = ps.opts.prune != 0;
+    // sorted output with 0 < topk <= 8192: the prune runs on the unsorted batch
+    // and only the kept entries are sorted (restored on every return path)
+    struct DeferSort {
+        PlanState &p;
+        ~DeferSort() { p.defer_sort = false; }
+    } defer_guard{ps};
+    ps.defer_sort = prune && ps.opts.sort_output && ps.opts.prune_topk > 0 && ps.opts.prune_topk <= 8192;
     // pieces: column ranges whose rows + values + colptr fit one host slot
     int64_t max_nnz = 0, max_cols = 0, max_col_bytes = 0, max_pnnz = 0;
     for (auto &b : ps.batches) {

@@ -787,7 +787,7 @@ template <class I, class V> struct Engine : EngineBase {
                 ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
                 ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
         }
-        if (ps.opts.sort_output)
+        if (ps.opts.sort_output && !ps.defer_sort)
             SPG_ST(sort_batch(cx, ps.colptr.as<int64_t>(), hc[b.c0], b.c0, b.c1, (I *)C->rowidx, (V *)C->vals,
                               b.heavy > 0 ? ps.items.as<HeavyItem>() : nullptr,
                               ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, st));
@@ -859,12 +859,15 @@ template <class I, class V> struct Engine : EngineBase {
         }
     }
 
-    static constexpr int64_t kPruneWsPerCol = 40;   // prune workspace bytes per column (PruneWs)
+    // prune workspace bytes per column (PruneWs: keep, sel, key, quota 8 B, row
+    // 4 B, mode 1 B, and the scan partials)
+    static constexpr int64_t kPruneWsPerCol = 40;
 
     // Prune step 1: kept count per column, the selections, and out_colptr =
     // exclusive scan of the counts (ncols + 1 entries, total last).
-    static spgemm_status prune_plan(const int64_t *colptr, const V *vals, int64_t ncols, V thr, int64_t topk,
-                                    PruneWs &ws, int64_t *out_colptr, int nsm, cudaStream_t st) {
+    static spgemm_status prune_plan(const int64_t *colptr, const I *rows, const V *vals, int64_t ncols, V thr,
+                                    int64_t topk, int tie_by_row, PruneWs &ws, int64_t *out_colptr, int nsm,
+                                    cudaStream_t st) {
         SPG_CK(ws.ensure(ncols));
         SPG_CK(cudaMemsetAsync(ws.nsel.p, 0, sizeof(unsigned long long), st));
         if (ncols > 0) {
@@ -872,9 +875,9 @@ template <class I, class V> struct Engine : EngineBase {
             k_prune_count<V><<<wb, 256, 0, st>>>(colptr, vals, ncols, thr, topk, ws.keep.as<int64_t>(),
                                                  ws.mode.as<int8_t>(), ws.sel.as<int64_t>(),
                                                  ws.nsel.as<unsigned long long>());
-            k_prune_select<V><<<(unsigned)nsm * 4, 512, 0, st>>>(colptr, vals, thr, topk, ws.sel.as<int64_t>(),
-                                                               ws.nsel.as<unsigned long long>(),
-                                                               ws.key.as<uint64_t>(), ws.quota.as<int64_t>());
+            k_prune_select<I, V><<<(unsigned)nsm * 4, 512, 0, st>>>(
+                colptr, rows, vals, thr, topk, ws.sel.as<int64_t>(), ws.nsel.as<unsigned long long>(),
+                ws.key.as<uint64_t>(), ws.quota.as<int64_t>(), tie_by_row, ws.row.as<uint32_t>());
         }
         SPG_CK(exclusive_scan_i64(ws.keep.as<int64_t>(), ncols, out_colptr, ws.part.as<int64_t>(), 1, st));
         SPG_CK(cudaGetLastError());
@@ -884,13 +887,13 @@ template <class I, class V> struct Engine : EngineBase {
     // Prune step 2: the kept entries, in input order, at out_colptr.
     template <class IO>
     static spgemm_status prune_fill(const int64_t *colptr, const I *rows, const V *vals, int64_t ncols, V thr,
-                                    PruneWs &ws, const int64_t *out_colptr, IO *orows, V *ovals,
+                                    int tie_by_row, PruneWs &ws, const int64_t *out_colptr, IO *orows, V *ovals,
                                     cudaStream_t st) {
         if (ncols <= 0) return SPGEMM_OK;
         const unsigned wb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ncols + 7) / 8, 1 << 20));
         k_prune_compact<I, V, IO><<<wb, 256, 0, st>>>(colptr, rows, vals, ncols, thr, ws.mode.as<int8_t>(),
-                                                      ws.key.as<uint64_t>(), ws.quota.as<int64_t>(),
-                                                      out_colptr, orows, ovals);
+                                                      ws.key.as<uint64_t>(), ws.quota.as<int64_t>(), tie_by_row,
+                                                      ws.row.as<uint32_t>(), out_colptr, orows, ovals);
         SPG_CK(cudaGetLastError());
         return SPGEMM_OK;
     }
@@ -919,7 +922,7 @@ template <class I, class V> struct Engine : EngineBase {
             SPG_CK(tmp.ensure(sizeof(int64_t) * (size_t)(n + 1)));
             ocp = tmp.as<int64_t>();
         }
-        SPG_ST(prune_plan(cp, (const V *)in->vals, n, thr, topk, ws, ocp, nsm, st));
+        SPG_ST(prune_plan(cp, (const I *)in->rowidx, (const V *)in->vals, n, thr, topk, 0, ws, ocp, nsm, st));
         if (count_only) {
             int64_t total = 0;
             SPG_CK(cudaMemcpyAsync(&total, ocp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -928,7 +931,7 @@ template <class I, class V> struct Engine : EngineBase {
             return SPGEMM_OK;
         }
         const int64_t *fin = (const int64_t *)out->colptr;
-        SPG_ST(prune_fill<I>(cp, (const I *)in->rowidx, (const V *)in->vals, n, thr, ws, fin, (I *)out->rowidx,
+        SPG_ST(prune_fill<I>(cp, (const I *)in->rowidx, (const V *)in->vals, n, thr, 0, ws, fin, (I *)out->rowidx,
                              (V *)out->vals, st));
         SPG_CK(cudaStreamSynchronize(st));   // the scratch buffers go out of scope
         return SPGEMM_OK;
@@ -938,10 +941,29 @@ template <class I, class V> struct Engine : EngineBase {
                               const void *vals, int64_t *ocolptr, void *orows, void *ovals, PruneWs &ws,
                               cudaStream_t st) override {
         const V thr = typed_threshold(ps.opts.prune_threshold);
-        SPG_ST(prune_plan(colptr, (const V *)vals, ncols, thr, ps.opts.prune_topk, ws, ocolptr, ps.nsm, st));
-        SPG_ST(prune_fill<I>(colptr, (const I *)rows, (const V *)vals, ncols, thr, ws, ocolptr, (I *)orows,
-                             (V *)ovals, st));
+        // sorted output with a small topk: prune the unsorted batch (ties to
+        // the smaller rows, the order sorting would give), then sort only
+        // the kept entries
+        const int tie_by_row = ps.defer_sort ? 1 : 0;
+        SPG_ST(prune_plan(colptr, (const I *)rows, (const V *)vals, ncols, thr, ps.opts.prune_topk, tie_by_row, ws,
+                          ocolptr, ps.nsm, st));
+        SPG_ST(prune_fill<I>(colptr, (const I *)rows, (const V *)vals, ncols, thr, tie_by_row, ws, ocolptr,
+                             (I *)orows, (V *)ovals, st));
         ps.timer.launches += 6;
+        if (ps.defer_sort) {
+            const int cap = (int)std::min<int64_t>(ps.opts.prune_topk, 8192);
+            const unsigned wbk = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ncols + 7) / 8, 1 << 20));
+            const unsigned bb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ncols, (int64_t)ps.nsm * 8));
+            k_sort_warp<I, V><<<wbk, 256, 0, st>>>(ocolptr, 0, 0, ncols, (I *)orows, (V *)ovals);
+            if (cap > 32)
+                k_sort_block<I, V, 1024><<<bb, 256, (int)(1024 * (4 + sizeof(V))), st>>>(
+                    ocolptr, 0, 0, ncols, 32, cap, (I *)orows, (V *)ovals);
+            if (cap > 1024)
+                k_sort_block<I, V, 8192><<<bb, 512, (int)(8192 * (4 + sizeof(V))), st>>>(
+                    ocolptr, 0, 0, ncols, 1024, cap, (I *)orows, (V *)ovals);
+            ps.timer.launches += 3;
+            SPG_CK(cudaGetLastError());
+        }
         return SPGEMM_OK;
     }
 

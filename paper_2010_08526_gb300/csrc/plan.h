@@ -48,7 +48,7 @@ int64_t scan_partials_len(int64_t n);
 // Workspace of the column prune (per column: kept count, mode, selection
 // list, selected key and tie quota; scan partials).
 struct PruneWs {
-    DevBuf keep, mode, sel, nsel, key, quota, part;
+    DevBuf keep, mode, sel, nsel, key, quota, part, row;
     cudaError_t ensure(int64_t ncols) {
         cudaError_t e;
         if ((e = keep.ensure(sizeof(int64_t) * (size_t)(ncols + 1))) != cudaSuccess) return e;
@@ -57,10 +57,16 @@ struct PruneWs {
         if ((e = nsel.ensure(sizeof(unsigned long long) * 2)) != cudaSuccess) return e;
         if ((e = key.ensure(sizeof(uint64_t) * (size_t)(ncols + 1))) != cudaSuccess) return e;
         if ((e = quota.ensure(sizeof(int64_t) * (size_t)(ncols + 1))) != cudaSuccess) return e;
+        if ((e = row.ensure(sizeof(uint32_t) * (size_t)(ncols + 1))) != cudaSuccess) return e;
         return part.ensure(sizeof(int64_t) * (size_t)scan_partials_len(ncols + 1));
     }
-    size_t bytes() const { return keep.bytes + mode.bytes + sel.bytes + nsel.bytes + key.bytes + quota.bytes + part.bytes; }
-    void release() { keep.release(); mode.release(); sel.release(); nsel.release(); key.release(); quota.release(); part.release(); }
+    size_t bytes() const {
+        return keep.bytes + mode.bytes + sel.bytes + nsel.bytes + key.bytes + quota.bytes + part.bytes + row.bytes;
+    }
+    void release() {
+        keep.release(); mode.release(); sel.release(); nsel.release(); key.release(); quota.release();
+        part.release(); row.release();
+    }
 };
 
 struct Tuning {
@@ -180,6 +186,7 @@ struct PlanState {
     int P = 0, Q = 0;        // numeric panels, symbolic panels
     int64_t Rs = 0;          // symbolic bitmap rows
     bool panels_built = false;
+    bool defer_sort = false;   // spgemm_run_batched sorts after its prune instead
     std::vector<Batch> batches;
     int64_t batch_cap = 0;
     int64_t bytes_per_nnz = 0;

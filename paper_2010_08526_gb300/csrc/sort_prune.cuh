@@ -221,15 +221,21 @@ __global__ void __launch_bounds__(256) k_prune_count(const int64_t *colptr, cons
 // values of a column crowd into few exponent bins, so one shared histogram
 // would serialise the atomics); the warp histograms are then summed and a
 // warp finds the digit with a suffix scan.
-template <class V>
-__global__ void __launch_bounds__(512) k_prune_select(const int64_t *colptr, const V *vals, V thr,
-                                                      int64_t topk, const int64_t *sel_list,
+// tie_by_row != 0: when more candidates share the selected key than the quota
+// keeps, a second radix pass over their rows (ascending) finds the largest
+// row kept (sel_row), so that equal values go to the smaller rows whatever
+// the storage order.
+template <class I, class V>
+__global__ void __launch_bounds__(512) k_prune_select(const int64_t *colptr, const I *rows, const V *vals,
+                                                      V thr, int64_t topk, const int64_t *sel_list,
                                                       const unsigned long long *nsel, uint64_t *sel_key,
-                                                      int64_t *sel_quota) {
+                                                      int64_t *sel_quota, int tie_by_row, uint32_t *sel_row) {
     __shared__ uint32_t hist[16][256];
     __shared__ uint32_t tot[256];
     __shared__ uint64_t s_prefix;
     __shared__ long long s_k;
+    __shared__ long long s_cnt;   // candidates in the selected bin of the last pass
+    __shared__ uint32_t s_rpre;   // row prefix of the tie pass
     constexpr int kBits = KeyBits<V>::v;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t ns = (int64_t)*nsel;
@@ -287,6 +293,7 @@ __global__ void __launch_bounds__(512) k_prune_select(const int64_t *colptr, con
                 if (lane == 0) {
                     s_prefix = prefix | ((uint64_t)(dg < 0 ? 0 : dg) << shift);
                     s_k = knew;
+                    s_cnt = dg < 0 ? 0 : (long long)tot[dg];
                 }
             }
             __syncthreads();
@@ -297,8 +304,64 @@ __global__ void __launch_bounds__(512) k_prune_select(const int64_t *colptr, con
             // number topk - s_k, so s_k equal keys are kept
             sel_key[j] = s_prefix;
             sel_quota[j] = s_k;
+            if (tie_by_row) sel_row[j] = 0xffffffffu;   // every tie kept
+            s_rpre = 0;
         }
+        // read before the barrier: after it thread 0 may start the next column
+        const bool row_pass = tie_by_row && s_cnt > s_k;
+        const uint64_t kkey = s_prefix;
         __syncthreads();
+        if (row_pass) {
+            // the s_k-th smallest row among the s_cnt ties (rows are distinct)
+            uint32_t rmask = 0;
+            for (int shift = 24; shift >= 0; shift -= 8) {
+                for (int i = threadIdx.x; i < 16 * 256; i += blockDim.x) (&hist[0][0])[i] = 0u;
+                __syncthreads();
+                const uint32_t rpre = s_rpre;
+                for (int64_t q = a + threadIdx.x; q < b; q += blockDim.x) {
+                    const V v = vals[q];
+                    if (!(v >= thr) || value_key(v) != kkey) continue;
+                    const uint32_t r = (uint32_t)rows[q];
+                    if ((r & rmask) != rpre) continue;
+                    atomicAdd(&hist[warp][(r >> shift) & 255u], 1u);
+                }
+                __syncthreads();
+                for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+                    uint32_t c = 0;
+                    for (int w = 0; w < nw; ++w) c += hist[w][d];
+                    tot[d] = c;
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    // lowest bin at which the count from the bottom reaches s_k
+                    const long long k = s_k;
+                    uint32_t c8[8];
+                    uint32_t mine = 0;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) { c8[i] = tot[lane * 8 + i]; mine += c8[i]; }
+                    const uint32_t incl = warp_incl_scan(mine);
+                    long long acc = (long long)(incl - mine);   // bins below this lane's range
+                    int dsel = -1;
+                    long long kk = 0;
+                    for (int i = 0; i < 8; ++i) {
+                        if (dsel < 0 && acc + (long long)c8[i] >= k) { dsel = lane * 8 + i; kk = k - acc; }
+                        acc += c8[i];
+                    }
+                    const unsigned found = __ballot_sync(SPG_FULL, dsel >= 0);
+                    const int src = found ? __ffs(found) - 1 : 0;
+                    const int dg = __shfl_sync(SPG_FULL, dsel, src);
+                    const long long knew = __shfl_sync(SPG_FULL, kk, src);
+                    if (lane == 0) {
+                        s_rpre = rpre | ((uint32_t)(dg < 0 ? 0 : dg) << shift);
+                        s_k = knew;
+                    }
+                }
+                __syncthreads();
+                rmask |= 255u << shift;
+            }
+            if (threadIdx.x == 0) sel_row[j] = s_rpre;
+            __syncthreads();
+        }
     }
 }
 
@@ -308,6 +371,7 @@ template <class I, class V, class IO>
 __global__ void __launch_bounds__(256) k_prune_compact(const int64_t *colptr, const I *rows, const V *vals,
                                                        int64_t ncols, V thr, const int8_t *mode,
                                                        const uint64_t *sel_key, const int64_t *sel_quota,
+                                                       int tie_by_row, const uint32_t *sel_row,
                                                        const int64_t *out_colptr, IO *out_rows, V *out_vals) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -318,6 +382,7 @@ __global__ void __launch_bounds__(256) k_prune_compact(const int64_t *colptr, co
         const bool sel = mode[j] != 0;
         const uint64_t kk = sel ? sel_key[j] : 0;
         int64_t quota = sel ? sel_quota[j] : 0;
+        const uint32_t rmax = (sel && tie_by_row) ? sel_row[j] : 0u;
         for (int64_t q0 = a; q0 < b; q0 += 32) {
             const int64_t q = q0 + lane;
             bool take = false, tie = false;
@@ -333,7 +398,9 @@ __global__ void __launch_bounds__(256) k_prune_compact(const int64_t *colptr, co
                     }
                 }
             }
-            if (sel) {
+            if (sel && tie_by_row) {
+                if (tie && (uint32_t)rows[q] <= rmax) take = true;
+            } else if (sel) {
                 const unsigned tb = __ballot_sync(SPG_FULL, tie);
                 const int before = __popc(tb & below);
                 if (tie && before < quota) take = true;

@@ -158,16 +158,20 @@ def test_prune_rejects_bad_arguments():
         spg.prune(C, float("nan"), 3)
 
 
-@pytest.mark.parametrize("kst", [1, 3])
-def test_run_batched_prunes_before_the_copy(kst):
+@pytest.mark.parametrize("kst,k", [(1, 7), (3, 7), (1, 40), (3, 2000), (1, 0), (3, 0)])
+def test_run_batched_prunes_before_the_copy(kst, k):
     """int64 path counts: the product is exact, so the streamed selection must
-    equal the oracle's bit for bit (and ties are everywhere)."""
+    equal the oracle's bit for bit (and ties are everywhere). With sorted
+    output and 0 < k <= 8192 the loop prunes the unsorted batch (ties go to
+    the smaller rows) and then sorts the kept entries: k = 7, 40 and 2000
+    reach the warp sort and both block sorts of that step; k = 0 keeps the
+    threshold only, after the full sort."""
     A = skewed(4000, 4000, 17, hubs=3, hub_deg=1500, base=6, dist="ones")
     Ad = to_dev(A)
     tun = spg.Tuning(hash_max_cap=256, panel_rows=1024)
     full = spg.spgemm(Ad, Ad, sort_output=True, tuning=tun, kstages=kst)
     torch.cuda.synchronize()
-    thr, k = 2.0, 7
+    thr = 2.0
     ref = oracle.prune(host_csc(full), thr, k)
     budget = A.bytes() * 3 + (1 << 20) + full.nnz * 12 // 2
     plan = spg.Plan(Ad, Ad, budget=budget, kstages=kst, tuning=tun, sort_output=True, prune=(thr, k),
@@ -190,7 +194,7 @@ def test_run_batched_prunes_before_the_copy(kst):
               np.concatenate([p[3] for p in pieces]).astype(np.int64),
               np.concatenate([p[4] for p in pieces]))
     assert pieces[0][0] == 0 and pieces[-1][1] == A.ncols
-    _same(got, ref, f"run_batched prune s={kst}")
+    _same(got, ref, f"run_batched prune s={kst} k={k}")
     assert ref.nnz < full.nnz                        # the prune did remove entries
 
 
