@@ -315,7 +315,8 @@ def run_gpu(args):
         kms = k0.elapsed_time(k1) / ks_steps
         kplan.check_errors()
         ks = {"value": 2 * F / (kms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": kms,
-              "stages": 4, "nbatches": kinfo["nbatches"], "unmerged_nnz": kinfo["unmerged_nnz"]}
+              "stages": 4, "nbatches": kinfo["nbatches"], "unmerged_nnz": kinfo["unmerged_nnz"],
+              "stage_buffer_nnz": kinfo["stage_buffer_nnz"], "merge": "end"}
         del kouts
         kplan.close()
         torch.cuda.empty_cache()
@@ -384,6 +385,7 @@ def run_gpu(args):
                                         note="the same product over the min-plus semiring")
         extras["min_plus"].pop("_counts")
         extras["protein_2M"] = bench_protein(spg, torch, args, dev)
+        extras["kmerge"] = bench_kmerge(spg, torch, args, A, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -460,11 +462,13 @@ def bench_multi(spg, torch, args):
             "tuning": autotune.describe([(best, 0.0)])[0], "autotune_trials": autotune.describe(trials)}
 
 
-def bench_step(spg, torch, args, A, dev, note, **plan_kw):
-    """Device time of one symbolic + numeric step of A*A with plan options."""
+def bench_step(spg, torch, args, A, dev, note, B=None, **plan_kw):
+    """Device time of one symbolic + numeric step of A*B (B = A by default)
+    with plan options."""
     st = torch.cuda.current_stream()
     Ad = spg.Csc.from_host(A, device=f"cuda:{dev}")
-    plan = spg.Plan(Ad, Ad, **plan_kw)
+    Bd = Ad if B is None else spg.Csc.from_host(B, device=f"cuda:{dev}")
+    plan = spg.Plan(Ad, Bd, **plan_kw)
     plan.set_timing(True)
     info = plan.symbolic()
     outs = [plan.alloc_batch(t) for t in range(plan.nbatches)]
@@ -492,10 +496,33 @@ def bench_step(spg, torch, args, A, dev, note, **plan_kw):
     plan.close()
     torch.cuda.empty_cache()
     F = int(info["flops"])
-    return {"value": 2 * F / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "flops_per_step": F,
-            "nnz_c": int(info["nnz_c"]), "nbatches": int(info["nbatches"]),
-            "phase_ms_per_step": {k: round(v / n, 3) for k, v in stats["ms"].items() if v},
-            "note": note, "_counts": cnt}
+    r = {"value": 2 * F / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "flops_per_step": F,
+         "nnz_c": int(info["nnz_c"]), "nbatches": int(info["nbatches"]),
+         "phase_ms_per_step": {k: round(v / n, 3) for k, v in stats["ms"].items() if v},
+         "note": note, "_counts": cnt}
+    if plan_kw.get("kstages", 1) > 1:
+        r["unmerged_nnz"] = int(info["unmerged_nnz"])
+        r["stage_buffer_nnz"] = int(info["stage_buffer_nnz"])
+    return r
+
+
+def bench_kmerge(spg, torch, args, A, dev):
+    """The k-split's two ways of summing the stage partials: merge at the end
+    (the paper's choice) against the incremental merge M_t = M_{t-1} + D_t.
+    On the headline product (4 stages), and on a saturated product where
+    every stage partial already fills most of C (8 stages): A 2048 x 262144
+    with 8 uniform rows per column, B 262144 x 16384 with 2048."""
+    out = {"rmat20_s4": bench_step(spg, torch, args, A, dev, kstages=4, merge="incremental",
+                                   note="incremental merge, headline product, 4 stages")}
+    out["rmat20_s4"].pop("_counts")
+    Ao = W.er_exact(2048, 262144, 8, 11, value_dtype=np.float32)
+    Bo = W.er_exact(262144, 16384, 2048, 12, value_dtype=np.float32)
+    for mode in ("end", "incremental"):
+        r = bench_step(spg, torch, args, Ao, dev, B=Bo, kstages=8, merge=mode,
+                       note=f"merge {mode}, saturated product, 8 stages")
+        r.pop("_counts")
+        out[f"overlap_s8_{mode}"] = r
+    return out
 
 
 def bench_protein(spg, torch, args, dev):

@@ -74,6 +74,16 @@ typedef enum { SPGEMM_F64 = 0, SPGEMM_F32 = 1, SPGEMM_INT64 = 2 } spgemm_value_t
  */
 typedef enum { SPGEMM_PLUS_TIMES = 0, SPGEMM_MIN_PLUS = 1 } spgemm_semiring_t;
 
+/* How the k-split (kstages = s > 1) sums a batch's stage partials D_0..D_{s-1}.
+ * AT_END: all s partials are kept and hash-merged once (the paper's choice,
+ * Sec. IV-D); a batch holds sum_t nnz(D_t) partial entries.
+ * INCREMENTAL: each stage is merged into the running sum as soon as it is
+ * produced, M_t = M_{t-1} + D_t (M_0 = D_0, M_{s-1} = C); a batch holds one
+ * stage partial and two running sums, max_t nnz(D_t) + 2 max_t nnz(M_t)
+ * entries (one running sum when s = 2), at the price of re-reading M_{t-1}
+ * in every merge and of s - 2 more symbolic passes that count nnz(M_t). */
+typedef enum { SPGEMM_MERGE_AT_END = 0, SPGEMM_MERGE_INCREMENTAL = 1 } spgemm_merge_t;
+
 /*
  * A CSC matrix: colptr[ncols+1] (type ptr_type), rowidx[nnz] and vals[nnz]
  * (types idx_type and val_type). For inputs ptr_type must equal idx_type.
@@ -132,6 +142,7 @@ typedef struct {
     int semiring;            /* spgemm_semiring_t (0 = plus-times); min-plus applies to the
                                 product, the k-stage merge and spgemm_run_batched, and
                                 spgemm_backward refuses it */
+    int merge_mode;          /* spgemm_merge_t (0 = merge at the end); used when kstages > 1 */
 } spgemm_opts;
 
 typedef struct spgemm_plan_s spgemm_plan;
@@ -147,6 +158,9 @@ typedef struct {
     int64_t bytes_per_nnz;    /* r = index bytes + value bytes */
     int64_t batch_cap_bytes;  /* bytes one batch may occupy on the device */
     int64_t heavy_columns;    /* columns handled by the dense row-panel accumulator */
+    int64_t stage_buffer_nnz; /* k-split: entries the largest batch's stage buffers hold
+                                 (sum_t nnz(D_t) merging at the end; max_t nnz(D_t) plus
+                                 the running sums merging incrementally); 0 when s = 1 */
 } spgemm_plan_info;
 
 /*

@@ -39,7 +39,7 @@ class SpgemmOpts(ctypes.Structure):
         ("host_slot_bytes", ctypes.c_size_t), ("host_slots", ctypes.c_int),
         ("sort_output", ctypes.c_int), ("tuning", ctypes.POINTER(SpgemmTuning)),
         ("prune", ctypes.c_int), ("prune_threshold", ctypes.c_double), ("prune_topk", ctypes.c_int64),
-        ("semiring", ctypes.c_int),
+        ("semiring", ctypes.c_int), ("merge_mode", ctypes.c_int),
     ]
 
 
@@ -49,6 +49,7 @@ class SpgemmPlanInfo(ctypes.Structure):
         ("nbatches", ctypes.c_int64), ("max_batch_nnz", ctypes.c_int64),
         ("max_batch_cols", ctypes.c_int64), ("bytes_per_nnz", ctypes.c_int64),
         ("batch_cap_bytes", ctypes.c_int64), ("heavy_columns", ctypes.c_int64),
+        ("stage_buffer_nnz", ctypes.c_int64),
     ]
 
 

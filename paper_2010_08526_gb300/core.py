@@ -102,8 +102,12 @@ class Tuning:
 _SEMIRINGS = {"plus_times": 0, "min_plus": 1}
 
 
+_MERGES = {"end": 0, "incremental": 1}
+
+
 def _opts(budget=None, kstages=1, tuning: Optional[Tuning] = None, ring_depth=0,
-          host_slot_bytes=0, host_slots=0, sort_output=False, prune=None, semiring="plus_times"):
+          host_slot_bytes=0, host_slots=0, sort_output=False, prune=None, semiring="plus_times",
+          merge="end"):
     o = C.SpgemmOpts()
     o.budget_bytes = int(budget or 0)
     o.kstages = int(kstages)
@@ -123,6 +127,9 @@ def _opts(budget=None, kstages=1, tuning: Optional[Tuning] = None, ring_depth=0,
     if semiring not in _SEMIRINGS:
         raise ValueError(f"unknown semiring {semiring!r}")
     o.semiring = _SEMIRINGS[semiring]
+    if merge not in _MERGES:
+        raise ValueError(f"unknown merge mode {merge!r}")
+    o.merge_mode = _MERGES[merge]
     keep = None
     if tuning is not None:
         keep = tuning.struct()
@@ -139,18 +146,21 @@ class Plan:
     def __init__(self, A: Csc, B: Csc, *, budget: Optional[int] = None, kstages: int = 1,
                  tuning: Optional[Tuning] = None, validate: bool = False, ring_depth: int = 0,
                  host_slot_bytes: int = 0, host_slots: int = 0, sort_output: bool = False,
-                 prune: Optional[tuple] = None, semiring: str = "plus_times",
+                 prune: Optional[tuple] = None, semiring: str = "plus_times", merge: str = "end",
                  stream: Optional[torch.cuda.Stream] = None):
         """sort_output: rows sorted inside every column of C. prune = (threshold,
         topk): run_batched prunes each batch on the device before the copy
         (see prune()). semiring: "plus_times" or "min_plus" (C(i,j) = min_k
-        A(i,k) + B(k,j), float values)."""
+        A(i,k) + B(k,j), float values). merge (kstages > 1): "end" keeps the
+        s stage partials of a batch and merges them once; "incremental"
+        merges each stage into the running sum as it is produced (less memory
+        when the stages overlap, more merge work)."""
         lib = load()
         self._lib = lib
         self.A, self.B = A, B
         self._sa, self._sb = A.struct(), B.struct()
         self._opts, self._tun = _opts(budget, kstages, tuning, ring_depth, host_slot_bytes,
-                                      host_slots, sort_output, prune, semiring)
+                                      host_slots, sort_output, prune, semiring, merge)
         h = ctypes.c_void_p()
         check(lib.spgemm_plan_create(ctypes.byref(self._sa), ctypes.byref(self._sb),
                                      ctypes.byref(self._opts), int(validate),
@@ -251,13 +261,15 @@ class Plan:
 
 def spgemm(A: Csc, B: Csc, *, budget: Optional[int] = None, kstages: int = 1,
            tuning: Optional[Tuning] = None, validate: bool = False, stream=None,
-           ptr_dtype=torch.int64, sort_output: bool = False, semiring: str = "plus_times") -> Csc:
+           ptr_dtype=torch.int64, sort_output: bool = False, semiring: str = "plus_times",
+           merge: str = "end") -> Csc:
     """C = A*B as one device CSC (batches computed one after another into
     slices of the full output). Rows inside columns are unsorted unless
     sort_output. ptr_dtype torch.int32 gives a colptr of the input index type
-    (if nnz(C) fits). semiring "min_plus": C(i,j) = min_k A(i,k) + B(k,j)."""
+    (if nnz(C) fits). semiring "min_plus": C(i,j) = min_k A(i,k) + B(k,j).
+    merge: how a k-split sums its stages ("end" or "incremental", see Plan)."""
     plan = Plan(A, B, budget=budget, kstages=kstages, tuning=tuning, validate=validate,
-                sort_output=sort_output, semiring=semiring, stream=stream)
+                sort_output=sort_output, semiring=semiring, merge=merge, stream=stream)
     try:
         info = plan.symbolic(stream)
         nnz = int(info["nnz_c"])

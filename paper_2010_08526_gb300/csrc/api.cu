@@ -25,7 +25,7 @@ size_t PlanState::workspace_bytes() const {
                             &off_sym, &off_num, &heavy_ord, &pcnt, &err, &scan_part, &wbytes,
                             &valid_flag, &ap_end, &ap_row, &ap_val, &apc_off, &apc_row, &apc_val, &stage_cnt, &stage_colptr,
                             &stage_pcnt, &merge_tmp, &drows, &dvals, &parts_tab, &items, &item_cnt,
-                            &item_off, &item_order};
+                            &item_off, &item_order, &pref_cnt, &pref_colptr, &pref_pcnt};
     size_t s = 0;
     for (auto *b : bufs) s += b->bytes;
     return s;
@@ -36,9 +36,10 @@ void PlanState::release_all() {
                       &off_sym, &off_num, &heavy_ord, &pcnt, &err, &scan_part, &wbytes,
                       &valid_flag, &ap_end, &ap_row, &ap_val, &apc_off, &apc_row, &apc_val, &stage_cnt, &stage_colptr,
                       &stage_pcnt, &merge_tmp, &drows, &dvals, &parts_tab, &items, &item_cnt,
-                      &item_off, &item_order};
+                      &item_off, &item_order, &pref_cnt, &pref_colptr, &pref_pcnt};
     for (auto *b : bufs) b->release();
     h_colptr.release();
+    h_pref_colptr.release();
     h_small.release();
     h_stage_colptr.release();
     h_parts.release();
@@ -114,6 +115,9 @@ spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B, const
     if (kst > 64) { set_error("kstages must be in [1, 64]"); return SPGEMM_ERR_INVALID; }
     if (opts && opts->prune && std::isnan(opts->prune_threshold)) {
         set_error("prune_threshold is NaN"); return SPGEMM_ERR_INVALID;
+    }
+    if (opts && opts->merge_mode != SPGEMM_MERGE_AT_END && opts->merge_mode != SPGEMM_MERGE_INCREMENTAL) {
+        set_error("unknown merge_mode"); return SPGEMM_ERR_INVALID;
     }
     if (opts && opts->semiring != SPGEMM_PLUS_TIMES) {
         if (opts->semiring != SPGEMM_MIN_PLUS) { set_error("unknown semiring"); return SPGEMM_ERR_INVALID; }
@@ -251,6 +255,7 @@ spgemm_status spgemm_plan_query(const spgemm_plan *plan, spgemm_plan_info *info)
     info->flops = ps.flops;
     info->nnz_c = ps.nnz_c;
     info->unmerged_nnz = ps.unmerged;
+    info->stage_buffer_nnz = ps.stage_buffer_nnz;
     info->nbatches = (int64_t)ps.batches.size();
     for (auto &b : ps.batches) {
         if (b.nnz > info->max_batch_nnz) info->max_batch_nnz = b.nnz;

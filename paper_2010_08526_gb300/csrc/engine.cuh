@@ -453,6 +453,10 @@ template <class I, class V> struct Engine : EngineBase {
         return a;
     }
 
+    static bool incremental(const PlanState &ps) {
+        return ps.s > 1 && ps.opts.merge_mode == SPGEMM_MERGE_INCREMENTAL;
+    }
+
     spgemm_status setup(PlanState &ps, cudaStream_t st) override {
         attrs();
         PD pd{};
@@ -527,6 +531,33 @@ template <class I, class V> struct Engine : EngineBase {
             }
             SPG_CK(cudaMemcpyAsync(ps.h_stage_colptr.p, ps.stage_colptr.p,
                                    sizeof(int64_t) * (size_t)ps.s * (n + 1), cudaMemcpyDeviceToHost, st));
+            // incremental merge: counts of the running sums M_u = D_0 + ... + D_u,
+            // i.e. the product over k in [0, k1_u), for u = 1..s-2 (M_0 is D_0,
+            // M_{s-1} is C), with panel counts for the heavy columns
+            if (incremental(ps) && ps.s > 2) {
+                const int nu = ps.s - 2;
+                SPG_CK(ps.pref_cnt.ensure(sizeof(int64_t) * (size_t)nu * (n + 1)));
+                SPG_CK(ps.pref_colptr.ensure(sizeof(int64_t) * (size_t)nu * (n + 1)));
+                SPG_CK(ps.h_pref_colptr.ensure(sizeof(int64_t) * (size_t)nu * (n + 1)));
+                if (ps.nheavy)
+                    SPG_CK(ps.pref_pcnt.ensure(sizeof(int32_t) * (size_t)nu * ps.nheavy * ps.P));
+                for (int u = 1; u <= nu; ++u) {
+                    const int64_t k1 = (int64_t)(u + 1) * ps.k / ps.s;
+                    int64_t *pc = ps.pref_cnt.as<int64_t>() + (size_t)(u - 1) * (n + 1);
+                    int32_t *pp = ps.nheavy ? ps.pref_pcnt.as<int32_t>() + (size_t)(u - 1) * ps.nheavy * ps.P
+                                            : nullptr;
+                    SPG_ST(sym_pass<SrcGemm<I, V>>(cx, gemm_args(ps, 0, k1), 0, n, ps.cnt.as<int64_t>(),
+                                                   nullptr, ps.tier.as<uint8_t>(), pc,
+                                                   ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(),
+                                                   nullptr, ps.heavy_ord.as<int32_t>(), nullptr, pp,
+                                                   nullptr, st));
+                    SPG_CK(exclusive_scan_i64(pc, n, ps.pref_colptr.as<int64_t>() + (size_t)(u - 1) * (n + 1),
+                                              ps.scan_part.as<int64_t>(), 1, st));
+                    cx.launched(3);
+                }
+                SPG_CK(cudaMemcpyAsync(ps.h_pref_colptr.p, ps.pref_colptr.p,
+                                       sizeof(int64_t) * (size_t)nu * (n + 1), cudaMemcpyDeviceToHost, st));
+            }
         }
         SPG_CK(cudaMemcpyAsync(ps.h_colptr.p, ps.colptr.p, sizeof(int64_t) * (n + 1),
                                cudaMemcpyDeviceToHost, st));
@@ -653,9 +684,33 @@ template <class I, class V> struct Engine : EngineBase {
                 ps.prune_prefix[(size_t)j + 1] = ps.prune_prefix[(size_t)j] + (k > 0 && c > k ? k : c);
             }
         }
+        // incremental merge: the stage buffers of columns [c, x) hold the
+        // largest stage partial D_t (t >= 1) and nm running sums, each sized
+        // by the largest M_u (u <= s-2; M_0 = D_0)
+        const bool inc = incremental(ps);
+        const int64_t *hp = (inc && ps.s > 2) ? ps.h_pref_colptr.as<int64_t>() : nullptr;
+        const int nm = ps.s > 2 ? 2 : 1;
+        auto inc_sizes = [&](int64_t c0, int64_t x, int64_t &dsz, int64_t &msz) {
+            dsz = 0;
+            for (int t = 1; t < ps.s; ++t)
+                dsz = std::max(dsz, hs[(size_t)t * (n + 1) + x] - hs[(size_t)t * (n + 1) + c0]);
+            msz = hs[x] - hs[c0];
+            for (int u = 1; u <= ps.s - 2; ++u)
+                msz = std::max(msz, hp[(size_t)(u - 1) * (n + 1) + x] - hp[(size_t)(u - 1) * (n + 1) + c0]);
+        };
         auto wprefix = [&](int64_t j) {
-            int64_t w = r * (hc[j] + unm(j)) + ptr_bytes * j;
+            int64_t w = r * (hc[j] + (inc ? 0 : unm(j))) + ptr_bytes * j;
             if (prune) w += r * ps.prune_prefix[(size_t)j] + (ptr_bytes + kPruneWsPerCol) * j;
+            return w;
+        };
+        // bytes of a batch over columns [c0, x)
+        auto wrange = [&](int64_t c0, int64_t x) {
+            int64_t w = wprefix(x) - wprefix(c0);
+            if (inc) {
+                int64_t d, m;
+                inc_sizes(c0, x, d, m);
+                w += r * (d + nm * m);
+            }
             return w;
         };
         int64_t c = 0;
@@ -666,21 +721,20 @@ template <class I, class V> struct Engine : EngineBase {
             ps.batches.push_back(b);
         }
         while (c < n) {
-            const int64_t limit = wprefix(c) + cap;
             int64_t lo = c, hi = n;
             while (lo < hi) {
                 const int64_t mid = lo + (hi - lo + 1) / 2;
-                if (wprefix(mid) <= limit) lo = mid; else hi = mid - 1;
+                if (wrange(c, mid) <= cap) lo = mid; else hi = mid - 1;
             }
             if (lo == c) {
-                set_error("column " + std::to_string(c) + " needs " +
-                          std::to_string(wprefix(c + 1) - wprefix(c)) +
+                set_error("column " + std::to_string(c) + " needs " + std::to_string(wrange(c, c + 1)) +
                           " B, more than one batch may hold (" + std::to_string(cap) + " B)");
                 return SPGEMM_ERR_BUDGET;
             }
             Batch b;
             b.c0 = c; b.c1 = lo; b.nnz = hc[lo] - hc[c];
             b.unmerged = hs ? unm(lo) - unm(c) : b.nnz;
+            if (inc) inc_sizes(c, lo, b.dsz, b.msz);
             b.pnnz = prune ? ps.prune_prefix[(size_t)lo] - ps.prune_prefix[(size_t)c] : b.nnz;
             ps.batches.push_back(b);
             c = lo;
@@ -692,7 +746,9 @@ template <class I, class V> struct Engine : EngineBase {
                 b.tc.resize(1);
                 tier_counts(hc, nullptr, b.c0, b.c1, capmax, b.tc[0], &b.heavy);
             } else {
-                b.tc.resize(ps.s + 1);
+                // [0] the final merge, [1 + t] stage t, [s + u] the merge into
+                // the running sum M_u (incremental, u = 1..s-2)
+                b.tc.resize(ps.s + 1 + (inc ? ps.s - 2 : 0));
                 tier_counts(hc, nullptr, b.c0, b.c1, capmax, b.tc[0], &b.heavy);
                 b.doff.resize(ps.s);
                 int64_t off = 0;
@@ -702,15 +758,24 @@ template <class I, class V> struct Engine : EngineBase {
                     b.doff[t] = off;
                     off += sc[b.c1] - sc[b.c0];
                 }
+                if (inc)
+                    for (int u = 1; u <= ps.s - 2; ++u)
+                        tier_counts(hp + (size_t)(u - 1) * (n + 1), hc, b.c0, b.c1, capmax, b.tc[ps.s + u],
+                                    nullptr);
             }
             total_unm += b.unmerged;
         }
         ps.unmerged = ps.s > 1 ? total_unm : ps.nnz_c;
+        ps.stage_buffer_nnz = 0;
+        if (ps.s > 1)
+            for (auto &b : ps.batches)
+                ps.stage_buffer_nnz = std::max(ps.stage_buffer_nnz, inc ? b.dsz + nm * b.msz : b.unmerged);
         return SPGEMM_OK;
     }
 
     // Partial buffers and per-batch part tables for the k-split merge.
     spgemm_status setup_stage_buffers(PlanState &ps, cudaStream_t st) {
+        if (incremental(ps)) return setup_incremental_buffers(ps, st);
         int64_t mx = 0;
         for (auto &b : ps.batches) mx = std::max(mx, b.unmerged);
         SPG_CK(ps.drows.ensure(sizeof(I) * (size_t)(mx + 1)));
@@ -738,6 +803,60 @@ template <class I, class V> struct Engine : EngineBase {
         return SPGEMM_OK;
     }
 
+    // Incremental merge: per batch, the stage buffer holds [D | M_a | M_b]:
+    // D (dsz entries) takes stage t >= 1, the running sums alternate between
+    // M_a and M_b (msz entries each; M_u lives in region u % 2). The part
+    // table has two parts per merge step t = 1..s-1: M_{t-1} and D_t.
+    spgemm_status setup_incremental_buffers(PlanState &ps, cudaStream_t st) {
+        SPG_CK(ps.drows.ensure(sizeof(I) * (size_t)(ps.stage_buffer_nnz + 1)));
+        SPG_CK(ps.dvals.ensure(sizeof(V) * (size_t)(ps.stage_buffer_nnz + 1)));
+        const size_t nb = ps.batches.size();
+        const int ns = ps.s - 1;
+        const size_t bytes = sizeof(PartDev<I, V>) * nb * ns * 2;
+        SPG_CK(ps.parts_tab.ensure(bytes));
+        SPG_CK(ps.h_parts.ensure(bytes));
+        auto *tab = ps.h_parts.as<PartDev<I, V>>();
+        for (size_t bi = 0; bi < nb; ++bi) {
+            const Batch &b = ps.batches[bi];
+            for (int t = 1; t <= ns; ++t) {
+                const int u = t - 1;
+                PartDev<I, V> &pm = tab[(bi * ns + (size_t)u) * 2];
+                PartDev<I, V> &pd = tab[(bi * ns + (size_t)u) * 2 + 1];
+                pm.colptr = run_colptr(ps, u);
+                pm.ptr64 = 1;
+                pm.sub = run_hcolptr(ps, u)[b.c0] - run_offset(b, u);
+                pm.rows = ps.drows.as<I>();
+                pm.vals = ps.dvals.as<V>();
+                pm.pcnt = run_pcnt(ps, u);
+                pd.colptr = ps.stage_colptr.as<int64_t>() + (size_t)t * (ps.n + 1);
+                pd.ptr64 = 1;
+                pd.sub = ps.h_stage_colptr.as<int64_t>()[(size_t)t * (ps.n + 1) + b.c0];
+                pd.rows = ps.drows.as<I>();
+                pd.vals = ps.dvals.as<V>();
+                pd.pcnt = ps.nheavy ? ps.stage_pcnt.as<int32_t>() + (size_t)t * ps.nheavy * ps.P : nullptr;
+            }
+        }
+        SPG_CK(cudaMemcpyAsync(ps.parts_tab.p, ps.h_parts.p, bytes, cudaMemcpyHostToDevice, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        return SPGEMM_OK;
+    }
+    // the running sum M_u (u <= s-2): device and host colptr, panel counts,
+    // and its offset in a batch's stage buffer
+    static const int64_t *run_colptr(const PlanState &ps, int u) {
+        return u == 0 ? ps.stage_colptr.as<int64_t>()
+                      : ps.pref_colptr.as<int64_t>() + (size_t)(u - 1) * (ps.n + 1);
+    }
+    static const int64_t *run_hcolptr(const PlanState &ps, int u) {
+        return u == 0 ? ps.h_stage_colptr.as<int64_t>()
+                      : ps.h_pref_colptr.as<int64_t>() + (size_t)(u - 1) * (ps.n + 1);
+    }
+    static const int32_t *run_pcnt(const PlanState &ps, int u) {
+        if (!ps.nheavy) return nullptr;
+        return u == 0 ? ps.stage_pcnt.as<int32_t>()
+                      : ps.pref_pcnt.as<int32_t>() + (size_t)(u - 1) * ps.nheavy * ps.P;
+    }
+    static int64_t run_offset(const Batch &b, int u) { return b.dsz + (int64_t)(u & 1) * b.msz; }
+
     // ---- numeric -------------------------------------------------------------
     spgemm_status numeric(PlanState &ps, int64_t t, spgemm_csc *C, cudaStream_t st) override {
         const Batch &b = ps.batches[(size_t)t];
@@ -753,6 +872,8 @@ template <class I, class V> struct Engine : EngineBase {
                 ps.heavy_ord.as<int32_t>(), ps.pcnt.as<int32_t>(), ps.tier.as<uint8_t>(),
                 ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
                 ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
+        } else if (incremental(ps)) {
+            SPG_ST(numeric_incremental(ps, cx, t, C, st));
         } else {
             const int64_t *hs = ps.h_stage_colptr.as<int64_t>();
             for (int s = 0; s < ps.s; ++s) {
@@ -794,6 +915,67 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(rebase_colptr(ps.colptr.as<int64_t>() + b.c0, b.c1 - b.c0, C->colptr,
                              C->ptr_type == SPGEMM_I64, st));
         cx.launched();
+        return SPGEMM_OK;
+    }
+
+    // Incremental k-split of batch bi: stage 0 goes to the running sum M_0;
+    // every later stage t goes to D and is hash-merged with M_{t-1} into M_t
+    // (into C for the last stage). Each merge is the same two-part merge as
+    // the final one, with the counts and panel counts of M_t.
+    spgemm_status numeric_incremental(PlanState &ps, Ctx &cx, int64_t bi, spgemm_csc *C, cudaStream_t st) {
+        const Batch &b = ps.batches[(size_t)bi];
+        const int64_t n = ps.n;
+        const int64_t *hc = ps.h_colptr.as<int64_t>();
+        const int64_t *hs = ps.h_stage_colptr.as<int64_t>();
+        const int ph_hash = cx.ph_hash, ph_dense = cx.ph_dense;
+        for (int s = 0; s < ps.s; ++s) {
+            const int64_t k0 = (int64_t)s * ps.k / ps.s, k1 = (int64_t)(s + 1) * ps.k / ps.s;
+            const int64_t *scp = ps.stage_colptr.as<int64_t>() + (size_t)s * (n + 1);
+            const int64_t *scnt = ps.stage_cnt.as<int64_t>() + (size_t)s * (n + 1);
+            // stage 0 straight into M_0's region, later stages into D (offset 0)
+            const int64_t at = s == 0 ? run_offset(b, 0) : 0;
+            NumOut<I, V> o{scp, hs[(size_t)s * (n + 1) + b.c0] - at, ps.drows.as<I>(), ps.dvals.as<V>()};
+            GA ga = gemm_args(ps, k0, k1);
+            const int32_t *spc = ps.nheavy ? ps.stage_pcnt.as<int32_t>() + (size_t)s * ps.nheavy * ps.P
+                                           : nullptr;
+            cx.ph_hash = ph_hash;
+            cx.ph_dense = ph_dense;
+            cx.stage_items = true;
+            SPG_ST((num_pass<SrcGemm<I, V>, SrcPanel<I, V>, SrcPanelRange<I, V>>(
+                cx, ga, ga, b.c0, b.c1, scnt, ps.cnt.as<int64_t>(), o, b.tc[1 + s].data(), b.heavy > 0,
+                ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(), ps.heavy_ord.as<int32_t>(), spc,
+                ps.tier.as<uint8_t>(), ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st,
+                ps.items.as<HeavyItem>(), ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items,
+                ps.item_order.as<int32_t>())));
+            if (s == 0) continue;
+            // M_s = M_{s-1} + D_s (sort-free hash merge, Sec. IV-D)
+            cx.ph_hash = kPhMerge;
+            cx.ph_dense = kPhMerge;
+            PA pa{ps.parts_tab.as<PartDev<I, V>>() + ((size_t)bi * (ps.s - 1) + (size_t)(s - 1)) * 2, 2, ps.m};
+            if (s < ps.s - 1) {
+                const int64_t *mcp = run_colptr(ps, s);
+                const int64_t *mcnt = ps.pref_cnt.as<int64_t>() + (size_t)(s - 1) * (n + 1);
+                NumOut<I, V> om{mcp, run_hcolptr(ps, s)[b.c0] - run_offset(b, s), ps.drows.as<I>(),
+                                ps.dvals.as<V>()};
+                cx.stage_items = true;
+                SPG_ST((num_pass<SrcParts<I, V>, SrcPartsPanel<I, V>, SrcPartsRange<I, V>>(
+                    cx, pa, pa, b.c0, b.c1, mcnt, ps.cnt.as<int64_t>(), om, b.tc[ps.s + s].data(),
+                    b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
+                    ps.heavy_ord.as<int32_t>(), run_pcnt(ps, s), ps.tier.as<uint8_t>(),
+                    ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
+                    ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
+            } else {
+                NumOut<I, V> oc{ps.colptr.as<int64_t>(), hc[b.c0], (I *)C->rowidx, (V *)C->vals};
+                cx.stage_items = false;
+                SPG_ST((num_pass<SrcParts<I, V>, SrcPartsPanel<I, V>, SrcPartsRange<I, V>>(
+                    cx, pa, pa, b.c0, b.c1, ps.cnt.as<int64_t>(), ps.cnt.as<int64_t>(), oc, b.tc[0].data(),
+                    b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
+                    ps.heavy_ord.as<int32_t>(), ps.pcnt.as<int32_t>(), ps.tier.as<uint8_t>(),
+                    ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
+                    ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
+            }
+        }
+        cx.stage_items = false;
         return SPGEMM_OK;
     }
 

@@ -82,6 +82,9 @@ struct Batch {
     int64_t nnz = 0;         // nnz(C) of the batch
     int64_t pnnz = 0;        // bound on the pruned batch (opts.prune)
     int64_t unmerged = 0;    // sum over stages of nnz(D_t) of the batch (s > 1)
+    // incremental merge (s > 1): entries of the largest stage partial D_t
+    // (t >= 1) and of the largest running sum M_u (u <= s - 2) of the batch
+    int64_t dsz = 0, msz = 0;
     // numeric hash-tier populations: [0] the product (s = 1) or the merge,
     // [1 + t] stage t (s > 1); host copies computed from the counts
     std::vector<std::array<int, 16>> tc;
@@ -165,10 +168,11 @@ struct PlanState {
     DevBuf ap_end, ap_row, ap_val;
     DevBuf apc_off, apc_row, apc_val;   // A grouped by panel within each column
     DevBuf stage_cnt, stage_colptr, stage_pcnt, drows, dvals, parts_tab;  // k-split
+    DevBuf pref_cnt, pref_colptr, pref_pcnt;   // incremental merge: nnz(M_u), u = 1..s-2
     DevBuf merge_tmp;
     DevBuf items, item_cnt, item_off, item_order;  // heavy work items (dense panels / hash ranges)
     int64_t n_items = 0;
-    HostBuf h_colptr, h_small, h_stage_colptr, h_parts;
+    HostBuf h_colptr, h_small, h_stage_colptr, h_parts, h_pref_colptr;
     std::vector<DevBuf> ring_col, ring_row, ring_val;   // spgemm_run_batched device ring
     std::vector<DevBuf> ring_pcol, ring_prow, ring_pval;  // pruned copies (opts.prune)
     std::vector<HostBuf> ring_hpc;                        // their colptrs on the host
@@ -181,6 +185,7 @@ struct PlanState {
     // symbolic results
     bool have_symbolic = false;
     int64_t flops = 0, nnz_c = 0, unmerged = 0;
+    int64_t stage_buffer_nnz = 0;   // entries of the largest batch's stage buffers (s > 1)
     int sym_hist[16] = {0};
     int nheavy = 0;          // symbolic heavy columns (dense path candidates)
     int P = 0, Q = 0;        // numeric panels, symbolic panels

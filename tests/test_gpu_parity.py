@@ -237,6 +237,120 @@ def test_ksplit_heavy_dense_merge(vt):
     check_product(A, A, f"ksplit heavy {vt.__name__}", kstages=4, tuning=tun)
 
 
+# ------------------------------------------- incremental (per-stage) merge
+
+def _stage_nnz(A, B, s):
+    """Oracle counts: nnz(D_t) per stage and nnz(M_u) of the running sums
+    M_u = D_0 + ... + D_u (the product over k in [0, k1_u))."""
+    kr = oracle.stage_ranges(A.ncols, s)
+    d = [int(oracle.symbolic(A, B, krange=r).sum()) for r in kr]
+    m = [int(oracle.symbolic(A, B, krange=(0, r[1])).sum()) for r in kr]
+    return d, m
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 7])
+def test_incremental_merge_equals_unsplit(s):
+    """merge="incremental" sums the stages as they come (M_t = M_{t-1} + D_t)
+    and must give the unsplit product; one batch holds the largest D_t
+    (t >= 1) plus one or two running sums sized by the largest M_u, u <= s-2."""
+    A = skewed(3000, 3000, 61, hubs=3, hub_deg=1200)
+    info = check_product(A, A, f"incremental s={s}", kstages=s, merge="incremental")
+    d, m = _stage_nnz(A, A, s)
+    assert info["unmerged_nnz"] == sum(d)
+    assert m[-1] == info["nnz_c"]
+    assert info["nbatches"] == 1
+    runs = [d[0]] + m[1:s - 1]
+    assert info["stage_buffer_nnz"] == max(d[1:]) + (2 if s > 2 else 1) * max(runs)
+
+
+@pytest.mark.parametrize("vt", [np.float32, np.int64])
+def test_incremental_heavy_dense_merge(vt):
+    """Heavy columns: the stage partials and the running sums are grouped by
+    the heavy items' panel ranges; dense-panel and hash-range merge items."""
+    dist = "normal" if vt != np.int64 else "ones"
+    A = skewed(5000, 5000, 71, hubs=4, hub_deg=2500, base=6, value_dtype=vt, dist=dist)
+    tun = spg.Tuning(hash_max_cap=256, panel_rows=1024)
+    info = check_product(A, A, f"incremental heavy {vt.__name__}", kstages=4, tuning=tun, merge="incremental")
+    assert info["heavy_columns"] > 0
+
+
+def _overlapping(m=240, k=3200, n=240, seed=5):
+    """Every stage partial is already most of C (cf high): 10 entries per
+    column of A, 160 per column of B, so D_t fills ~2/3 of each column."""
+    rng = np.random.default_rng(seed)
+    ra = np.concatenate([rng.choice(m, 10, replace=False) for _ in range(k)])
+    A = from_coo(m, k, ra, np.repeat(np.arange(k), 10), rng.standard_normal(ra.size))
+    rb = np.concatenate([rng.choice(k, 160, replace=False) for _ in range(n)])
+    B = from_coo(k, n, rb, np.repeat(np.arange(n), 160), rng.standard_normal(rb.size))
+    return shuffle_within_columns(A, seed + 1), shuffle_within_columns(B, seed + 2)
+
+
+def test_incremental_merge_needs_less_memory_when_stages_overlap():
+    A, B = _overlapping()
+    s = 8
+    end = check_product(A, B, "overlap end", kstages=s)
+    inc = check_product(A, B, "overlap incremental", kstages=s, merge="incremental")
+    d, m = _stage_nnz(A, B, s)
+    assert end["stage_buffer_nnz"] == sum(d)
+    assert inc["stage_buffer_nnz"] == max(d[1:]) + 2 * max([d[0]] + m[1:s - 1])
+    assert inc["stage_buffer_nnz"] < 0.6 * end["stage_buffer_nnz"]
+    # a budget whose batch cap (half of what the inputs and the workspace
+    # leave, two batches in flight) just holds C plus the incremental buffers
+    # in one batch: the s partials do not fit, so merging at the end needs
+    # more batches
+    Ad, Bd = to_dev(A), to_dev(B)
+    big = 1 << 30
+    probe = spg.Plan(Ad, Bd, budget=big, kstages=s, merge="incremental")
+    cap0 = probe.symbolic()["batch_cap_bytes"]
+    probe.close()
+    r = 12
+    target = r * (inc["nnz_c"] + inc["stage_buffer_nnz"]) + 8 * (B.ncols + 1) + 4096
+    budget = big - 2 * (cap0 - target)
+    pe = spg.Plan(Ad, Bd, budget=budget, kstages=s)
+    pi = spg.Plan(Ad, Bd, budget=budget, kstages=s, merge="incremental")
+    ne, ni = pe.symbolic()["nbatches"], pi.symbolic()["nbatches"]
+    pe.close(); pi.close()
+    assert ni == 1 and ne > 1, (ni, ne)
+
+
+@pytest.mark.parametrize("kst", [3, 5])
+def test_incremental_merge_over_batches(kst):
+    """Several batches (budget-limited) through plan.numeric and run_batched."""
+    A = skewed(4000, 4000, 83, hubs=3, hub_deg=1500, base=6)
+    ref, ab = oracle.spgemm(A, A, with_absterm=True)
+    Ad = to_dev(A)
+    tun = spg.Tuning(hash_max_cap=256, panel_rows=1024)
+    budget = A.bytes() * 2 + (4 << 20) + ref.nnz * 12
+    plan = spg.Plan(Ad, Ad, budget=budget, kstages=kst, tuning=tun, merge="incremental",
+                    host_slot_bytes=1 << 16, host_slots=2)
+    info = plan.symbolic()
+    assert info["nbatches"] >= 2
+    pieces = []
+
+    def sink(batch, c0, c1, arrs):
+        cp, ri, va = arrs
+        pieces.append((c0, c1, cp.copy(), ri.copy(), va.copy()))
+        return 0
+
+    spg.run_batched(plan, sink)
+    outs = [host_csc(plan.numeric(t)) for t in range(plan.nbatches)]
+    torch.cuda.synchronize()
+    plan.close()
+
+    def assemble(chunks):
+        colptr = [0]
+        for cp in chunks[0]:
+            colptr.extend((np.asarray(cp, np.int64)[1:] + colptr[-1]).tolist())
+        return CSC(A.nrows, A.ncols, np.array(colptr, np.int64),
+                   np.concatenate(chunks[1]).astype(np.int64), np.concatenate(chunks[2]))
+
+    got = assemble(([p[2] for p in pieces], [p[3] for p in pieces], [p[4] for p in pieces]))
+    assert pieces[0][0] == 0 and pieces[-1][1] == A.ncols
+    assert_matches(got, ref, ab, label=f"incremental run_batched s={kst}")
+    got2 = assemble(([o.colptr for o in outs], [o.rowidx for o in outs], [o.vals for o in outs]))
+    assert_matches(got2, ref, ab, label=f"incremental numeric s={kst}")
+
+
 def test_merge_api():
     parts = [rand_csc(700, 300, 0.02, 80 + t) for t in range(4)]
     M = spg.merge([to_dev(p) for p in parts])
