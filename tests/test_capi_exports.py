@@ -50,3 +50,38 @@ def test_product_path_fails_loudly_without_library(tmp_path):
             _capi.load(str(tmp_path / "missing.so"))
         finally:
             _capi._LIB = _capi._LIB_saved
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror of a header struct has the C compiler's size and
+    field offsets (a field added on one side only would shift the rest)."""
+    import shutil
+    import subprocess
+
+    import pytest
+    from paper_2010_08526_gb300 import _capi as C
+
+    gcc = shutil.which("gcc")
+    nvcc = shutil.which("nvcc")
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "include") if nvcc else "/usr/local/cuda/include"
+    if not gcc or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime_api.h")):
+        pytest.skip("needs gcc and the CUDA headers")
+    structs = {"spgemm_csc": C.SpgemmCsc, "spgemm_tuning": C.SpgemmTuning, "spgemm_opts": C.SpgemmOpts,
+               "spgemm_plan_info": C.SpgemmPlanInfo, "spgemm_stats": C.SpgemmStats}
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "spgemm.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        src.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            src.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    src.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, str(c), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, f"{cname}.{f}"
