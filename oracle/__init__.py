@@ -85,7 +85,7 @@ class _Held:
     def __init__(self, a: CSC, vtype: int):
         self.colptr = np.ascontiguousarray(a.colptr, dtype=np.int64)
         self.rowidx = np.ascontiguousarray(a.rowidx, dtype=np.int64)
-        vt = np.int64 if vtype == 2 else np.float64
+        vt = np.int64 if vtype in (2, 5) else np.float64
         self.vals = np.ascontiguousarray(a.vals, dtype=vt)
         self.s = _OCSC(a.nrows, a.ncols, self.colptr.ctypes.data, self.rowidx.ctypes.data,
                        self.vals.ctypes.data)
@@ -129,6 +129,8 @@ def _sr_vtype(dtype, semiring: str) -> int:
         if _vtype(dtype) != 0:
             raise ValueError("min_plus is defined for floating-point values")
         return 3
+    if semiring == "or_and":
+        return 5 if _vtype(dtype) == 2 else 4
     raise ValueError(f"unknown semiring {semiring!r}")
 
 
@@ -138,7 +140,8 @@ def spgemm(A: CSC, B: CSC, krange=None, cols=None, with_absterm: bool = False,
 
     semiring "min_plus": C(i, j) = min over k of A(i, k) + B(k, j) on the same
     structure (the algorithms hold over any semiring, Sec. II); NaN products
-    are ignored.
+    are ignored. "or_and": C(i, j) = 1 if A(i, k) != 0 and B(k, j) != 0 for
+    some k, else 0 (Boolean values in the input's value type).
 
     Returns a CSC (int64 indices, float64 or int64 values, rows sorted) and,
     if asked, the per-entry rounding-error scale: sum |products| (plus-times)
@@ -157,7 +160,7 @@ def spgemm(A: CSC, B: CSC, krange=None, cols=None, with_absterm: bool = False,
     np.cumsum(cnt, out=colptr[1:])
     nnz = int(colptr[-1])
     rowidx = np.zeros(nnz, dtype=np.int64)
-    vals = np.zeros(nnz, dtype=np.int64 if vt == 2 else np.float64)
+    vals = np.zeros(nnz, dtype=np.int64 if vt in (2, 5) else np.float64)
     absterm = np.zeros(nnz, dtype=np.float64) if (with_absterm and vt in (0, 3)) else None
     lib.oracle_spgemm(ctypes.byref(ha.s), ctypes.byref(hb.s), vt, k0, k1, c0, c1,
                       _ptr(colptr), _ptr(rowidx), _ptr(vals),
@@ -169,7 +172,7 @@ def spgemm(A: CSC, B: CSC, krange=None, cols=None, with_absterm: bool = False,
 def merge(parts, semiring: str = "plus_times") -> CSC:
     """Add entries of equal (row, col) across ``parts`` (Sec. III-A merge;
     column j of the result formed from column j of every part, Sec. IV-D);
-    "min_plus" takes their minimum."""
+    "min_plus" takes their minimum, "or_and" their OR (1 if one is nonzero)."""
     parts = list(parts)
     if not parts:
         raise ValueError("no parts")
@@ -185,7 +188,7 @@ def merge(parts, semiring: str = "plus_times") -> CSC:
     lib.oracle_merge(arr, len(parts), vt, 1, _ptr(colptr), None, None)
     nnz = int(colptr[-1])
     rowidx = np.zeros(nnz, dtype=np.int64)
-    vals = np.zeros(nnz, dtype=np.int64 if vt == 2 else np.float64)
+    vals = np.zeros(nnz, dtype=np.int64 if vt in (2, 5) else np.float64)
     lib.oracle_merge(arr, len(parts), vt, 0, _ptr(colptr), _ptr(rowidx), _ptr(vals))
     return CSC(m, n, colptr, rowidx, vals)
 

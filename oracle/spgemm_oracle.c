@@ -12,7 +12,11 @@
  *     wrapper and accumulated in float64), vtype 2 = int64 accumulated with
  *     two's-complement wrap-around (done in uint64_t), vtype 3 = float64 over
  *     the min-plus semiring (the paper's algorithms hold over any semiring,
- *     Sec. II): a (x) b = a + b, (+) = min, NaN products ignored (fmin).
+ *     Sec. II): a (x) b = a + b, (+) = min, NaN products ignored (fmin);
+ *     vtype 4 (float64 storage) and vtype 5 (int64 storage) = the Boolean
+ *     or-and semiring: a value is true when it is nonzero (-0.0 is false, NaN
+ *     true), a (x) b = a AND b, (+) = OR, and an entry of C holds 1 when one
+ *     of its products is true, else 0.
  *   - Rows inside an input column may be in any order; (row, col) is unique.
  *   - Output columns are sorted ascending by row; numerically-zero sums are
  *     kept as structural nonzeros (a nonzero of C is any (i, j) reached by at
@@ -147,6 +151,12 @@ void oracle_spgemm(const ocsc *A, const ocsc *B, int vtype, int64_t k0, int64_t 
                         spa[i] = fmin(spa[i], a + b);
                         const double s = fabs(a) + fabs(b);
                         if (s > spa_abs[i]) spa_abs[i] = s;
+                    } else if (vtype == 4 || vtype == 5) {
+                        const int a = vtype == 4 ? ((const double *)A->vals)[q] != 0.0
+                                                 : ((const int64_t *)A->vals)[q] != 0;
+                        const int b = vtype == 4 ? ((const double *)B->vals)[p] != 0.0
+                                                 : ((const int64_t *)B->vals)[p] != 0;
+                        if (a && b) spa_i[i] = 1;
                     } else {
                         double t = ((const double *)A->vals)[q] * ((const double *)B->vals)[p];
                         spa[i] += t;
@@ -157,7 +167,8 @@ void oracle_spgemm(const ocsc *A, const ocsc *B, int vtype, int64_t k0, int64_t 
             qsort(rowidx_out + base, (size_t)len, sizeof(int64_t), cmp_i64);
             for (int64_t t = 0; t < len; ++t) {
                 int64_t i = rowidx_out[base + t];
-                if (vtype == 2) ((int64_t *)vals_out)[base + t] = (int64_t)spa_i[i];
+                if (vtype == 2 || vtype == 5) ((int64_t *)vals_out)[base + t] = (int64_t)spa_i[i];
+                else if (vtype == 4) ((double *)vals_out)[base + t] = (double)spa_i[i];
                 else {
                     ((double *)vals_out)[base + t] = spa[i];
                     if (absterm_out) absterm_out[base + t] = spa_abs[i];
@@ -212,12 +223,15 @@ void oracle_merge(const ocsc *parts, int nparts, int vtype, int cnt_only,
                     }
                     if (vtype == 2) spa_i[i] += (uint64_t)((const int64_t *)parts[t].vals)[q];
                     else if (vtype == 3) spa[i] = fmin(spa[i], ((const double *)parts[t].vals)[q]);
+                    else if (vtype == 4) { if (((const double *)parts[t].vals)[q] != 0.0) spa_i[i] = 1; }
+                    else if (vtype == 5) { if (((const int64_t *)parts[t].vals)[q] != 0) spa_i[i] = 1; }
                     else spa[i] += ((const double *)parts[t].vals)[q];
                 }
             qsort(rowidx_out + base, (size_t)len, sizeof(int64_t), cmp_i64);
             for (int64_t t = 0; t < len; ++t) {
                 int64_t i = rowidx_out[base + t];
-                if (vtype == 2) ((int64_t *)vals_out)[base + t] = (int64_t)spa_i[i];
+                if (vtype == 2 || vtype == 5) ((int64_t *)vals_out)[base + t] = (int64_t)spa_i[i];
+                else if (vtype == 4) ((double *)vals_out)[base + t] = (double)spa_i[i];
                 else ((double *)vals_out)[base + t] = spa[i];
             }
         }

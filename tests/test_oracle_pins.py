@@ -506,3 +506,58 @@ def test_minplus_identity_and_nan_and_stages():
     merged = oracle.merge(parts, semiring="min_plus")
     assert np.array_equal(merged.colptr, full.colptr) and np.array_equal(merged.rowidx, full.rowidx)
     assert np.array_equal(merged.vals, full.vals)
+
+
+# ---------------------------------------------------------------- or-and
+def _with_false_entries(A: CSC, seed, as_int=False):
+    """About a third of the stored values set to false (0, and -0.0 for
+    floats), one to NaN (true): explicit zeros are stored entries that
+    carry no truth."""
+    rng = np.random.default_rng(seed)
+    v = A.vals.astype(np.int64 if as_int else np.float64).copy()
+    z = rng.random(v.size) < 0.35
+    v[z] = 0
+    if not as_int:
+        v[z & (rng.random(v.size) < 0.5)] = -0.0
+        v[np.flatnonzero(~z)[:1]] = np.nan
+    return CSC(A.nrows, A.ncols, A.colptr, A.rowidx, v)
+
+
+@pytest.mark.parametrize("seed,as_int", [(1, False), (2, False), (3, True), (4, True)])
+def test_orand_matches_dense_boolean_product(seed, as_int):
+    """Or-and (the algorithms hold over any semiring, Sec. II): on the
+    structure of the product, C(i,j) = 1 iff some k has A(i,k) != 0 and
+    B(k,j) != 0 -- a dense integer product of the truth matrices."""
+    A = _with_false_entries(rand_csc(25, 18, 0.3, seed), seed + 20, as_int)
+    B = _with_false_entries(rand_csc(18, 21, 0.3, seed + 10), seed + 30, as_int)
+    C = oracle.spgemm(A, B, semiring="or_and")
+
+    def truth(X):
+        d = np.zeros((X.nrows, X.ncols), np.int64)
+        cx = np.repeat(np.arange(X.ncols), X.col_counts())
+        d[X.rowidx.astype(np.int64), cx] = (X.vals != 0).astype(np.int64)   # NaN != 0 is true
+        return d
+
+    struct = dense_structure(A) @ dense_structure(B) > 0
+    val = (truth(A) @ truth(B)) > 0
+    assert np.array_equal(dense_structure(C) > 0, struct)
+    cc = np.repeat(np.arange(C.ncols), C.col_counts())
+    assert np.array_equal(C.vals, val[C.rowidx, cc].astype(C.vals.dtype))
+    assert C.vals.dtype == (np.int64 if as_int else np.float64)
+    assert 0 < int((C.vals == 0).sum()) < C.nnz          # both truth values occur
+
+
+def test_orand_stages_merge_and_all_true_inputs():
+    A = _with_false_entries(rand_csc(30, 30, 0.2, 7), 9)
+    B = _with_false_entries(rand_csc(30, 40, 0.2, 8), 10)
+    full = oracle.spgemm(A, B, semiring="or_and")
+    parts = [oracle.spgemm(A, B, krange=r, semiring="or_and") for r in oracle.stage_ranges(30, 3)]
+    merged = oracle.merge(parts, semiring="or_and")
+    assert np.array_equal(merged.colptr, full.colptr) and np.array_equal(merged.rowidx, full.rowidx)
+    assert np.array_equal(merged.vals, full.vals)
+    # inputs without false entries: every entry of C is true, on C's structure
+    P = rand_csc(30, 30, 0.2, 11)
+    Q = rand_csc(30, 40, 0.2, 12)
+    Cb = oracle.spgemm(P, Q, semiring="or_and")
+    assert np.array_equal(Cb.colptr[1:] - Cb.colptr[:-1], oracle.symbolic(P, Q))
+    assert np.all(Cb.vals == 1.0)
