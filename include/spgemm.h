@@ -69,10 +69,12 @@ typedef enum { SPGEMM_F64 = 0, SPGEMM_F32 = 1, SPGEMM_INT64 = 2 } spgemm_value_t
  * The semiring of the product (the paper's algorithms hold over any semiring,
  * Sec. II). PLUS_TIMES: C(i,j) = sum_k A(i,k) B(k,j). MIN_PLUS (float64 and
  * float32 values): C(i,j) = min_k A(i,k) + B(k,j), NaN sums ignored (a column
- * entry whose every candidate is NaN holds +infinity); the structure of C is
- * the same in both.
+ * entry whose every candidate is NaN holds +infinity). OR_AND (any value
+ * type, Boolean): a value is true when nonzero (-0.0 false, NaN true);
+ * C(i,j) = 1 if A(i,k) and B(k,j) are both true for some k, else 0, in the
+ * value type. The structure of C is the same in all three.
  */
-typedef enum { SPGEMM_PLUS_TIMES = 0, SPGEMM_MIN_PLUS = 1 } spgemm_semiring_t;
+typedef enum { SPGEMM_PLUS_TIMES = 0, SPGEMM_MIN_PLUS = 1, SPGEMM_OR_AND = 2 } spgemm_semiring_t;
 
 /* How the k-split (kstages = s > 1) sums a batch's stage partials D_0..D_{s-1}.
  * AT_END: all s partials are kept and hash-merged once (the paper's choice,
@@ -139,9 +141,9 @@ typedef struct {
                                 below (the batch consumer of Sec. III / V-F); 0: off */
     double prune_threshold;  /* keep values >= this (-INFINITY: no threshold) */
     int64_t prune_topk;      /* then at most this many per column (<= 0: no limit) */
-    int semiring;            /* spgemm_semiring_t (0 = plus-times); min-plus applies to the
-                                product, the k-stage merge and spgemm_run_batched, and
-                                spgemm_backward refuses it */
+    int semiring;            /* spgemm_semiring_t (0 = plus-times); min-plus and or-and apply
+                                to the product, the k-stage merge and spgemm_run_batched,
+                                and spgemm_backward refuses them */
     int merge_mode;          /* spgemm_merge_t (0 = merge at the end); used when kstages > 1 */
 } spgemm_opts;
 

@@ -20,10 +20,13 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr"]
 
 SOURCES = [
-    "api.cu", "engines.cu", "util_kernels.cu", "batched.cu", "multi.cu", "noalloc.cu", "transpose.cu",
+    # the engine instantiations take longest: listed first so they start first
     "inst_i32_f64.cu", "inst_i32_f32.cu", "inst_i32_i64v.cu",
     "inst_i64_f64.cu", "inst_i64_f32.cu", "inst_i64_i64v.cu",
     "inst_i32_mpf32.cu", "inst_i32_mpf64.cu", "inst_i64_mpf32.cu", "inst_i64_mpf64.cu",
+    "inst_i32_oaf32.cu", "inst_i32_oaf64.cu", "inst_i32_oai64.cu",
+    "inst_i64_oaf32.cu", "inst_i64_oaf64.cu", "inst_i64_oai64.cu",
+    "api.cu", "engines.cu", "util_kernels.cu", "batched.cu", "multi.cu", "noalloc.cu", "transpose.cu",
 ]
 
 

@@ -99,7 +99,7 @@ class Tuning:
         return t
 
 
-_SEMIRINGS = {"plus_times": 0, "min_plus": 1}
+_SEMIRINGS = {"plus_times": 0, "min_plus": 1, "or_and": 2}
 
 
 _MERGES = {"end": 0, "incremental": 1}
@@ -150,8 +150,9 @@ class Plan:
                  stream: Optional[torch.cuda.Stream] = None):
         """sort_output: rows sorted inside every column of C. prune = (threshold,
         topk): run_batched prunes each batch on the device before the copy
-        (see prune()). semiring: "plus_times" or "min_plus" (C(i,j) = min_k
-        A(i,k) + B(k,j), float values). merge (kstages > 1): "end" keeps the
+        (see prune()). semiring: "plus_times", "min_plus" (C(i,j) = min_k
+        A(i,k) + B(k,j), float values) or "or_and" (Boolean: 1 where some k
+        has A(i,k) != 0 and B(k,j) != 0, else 0, any value type). merge (kstages > 1): "end" keeps the
         s stage partials of a batch and merges them once; "incremental"
         merges each stage into the running sum as it is produced (less memory
         when the stages overlap, more merge work)."""
@@ -266,7 +267,8 @@ def spgemm(A: Csc, B: Csc, *, budget: Optional[int] = None, kstages: int = 1,
     """C = A*B as one device CSC (batches computed one after another into
     slices of the full output). Rows inside columns are unsorted unless
     sort_output. ptr_dtype torch.int32 gives a colptr of the input index type
-    (if nnz(C) fits). semiring "min_plus": C(i,j) = min_k A(i,k) + B(k,j).
+    (if nnz(C) fits). semiring "min_plus": C(i,j) = min_k A(i,k) + B(k,j);
+    "or_and": the Boolean product (1 or 0 on C's structure).
     merge: how a k-split sums its stages ("end" or "incremental", see Plan)."""
     plan = Plan(A, B, budget=budget, kstages=kstages, tuning=tuning, validate=validate,
                 sort_output=sort_output, semiring=semiring, merge=merge, stream=stream)

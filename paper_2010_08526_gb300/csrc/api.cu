@@ -119,7 +119,7 @@ spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B, const
     if (opts && opts->merge_mode != SPGEMM_MERGE_AT_END && opts->merge_mode != SPGEMM_MERGE_INCREMENTAL) {
         set_error("unknown merge_mode"); return SPGEMM_ERR_INVALID;
     }
-    if (opts && opts->semiring != SPGEMM_PLUS_TIMES) {
+    if (opts && opts->semiring != SPGEMM_PLUS_TIMES && opts->semiring != SPGEMM_OR_AND) {
         if (opts->semiring != SPGEMM_MIN_PLUS) { set_error("unknown semiring"); return SPGEMM_ERR_INVALID; }
         if (A->val_type == SPGEMM_INT64) {
             set_error("the min-plus semiring needs floating-point values"); return SPGEMM_ERR_INVALID;

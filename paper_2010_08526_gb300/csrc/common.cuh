@@ -99,6 +99,53 @@ template <> __device__ __forceinline__ void atomic_add_v<MinPlus<double>>(MinPlu
     else atomicMax(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double_as_longlong(f));
 }
 
+// ---- or-and (Boolean) semiring values -------------------------------------
+// OrAnd<T> stores the plain float / double / int64 bits. A value is true when
+// it is nonzero (-0.0 is false, NaN true); a (x) b = a AND b and (+) = OR,
+// each written as 0 or 1 of type T. Integer literals name the identities:
+// V(0) = false clears an accumulator, V(1) = true scales a merged partial.
+template <class T> struct OrAnd {
+    T v;
+    OrAnd() = default;
+    __host__ __device__ constexpr OrAnd(int lit) : v(lit != 0 ? T(1) : T(0)) {}
+    __host__ __device__ static constexpr OrAnd raw(T x) {
+        OrAnd o(0);
+        o.v = x;
+        return o;
+    }
+    __host__ __device__ friend bool operator>=(OrAnd a, OrAnd b) { return a.v >= b.v; }
+    __host__ __device__ friend bool operator==(OrAnd a, OrAnd b) { return a.v == b.v; }
+};
+template <class T> struct IsOrAnd { static constexpr bool v = false; };
+template <class T> struct IsOrAnd<OrAnd<T>> { static constexpr bool v = true; };
+
+// the stored scalar of a value type (the wrapped one for semiring wrappers)
+template <class V> struct Storage { using type = V; };
+template <class F> struct Storage<MinPlus<F>> { using type = F; };
+template <class T> struct Storage<OrAnd<T>> { using type = T; };
+
+template <> __device__ __forceinline__ OrAnd<float> mul_v<OrAnd<float>>(OrAnd<float> a, OrAnd<float> b) {
+    return OrAnd<float>::raw((a.v != 0.0f && b.v != 0.0f) ? 1.0f : 0.0f);
+}
+template <> __device__ __forceinline__ OrAnd<double> mul_v<OrAnd<double>>(OrAnd<double> a, OrAnd<double> b) {
+    return OrAnd<double>::raw((a.v != 0.0 && b.v != 0.0) ? 1.0 : 0.0);
+}
+template <> __device__ __forceinline__ OrAnd<int64_t> mul_v<OrAnd<int64_t>>(OrAnd<int64_t> a, OrAnd<int64_t> b) {
+    return OrAnd<int64_t>::raw((a.v != 0 && b.v != 0) ? 1 : 0);
+}
+// OR: a true operand sets the accumulator to the bits of 1 with an integer
+// atomicOr; the accumulator starts as the bits of 0 and only ever receives
+// the bits of 1, so it holds exactly 0 or 1. A false operand changes nothing.
+template <> __device__ __forceinline__ void atomic_add_v<OrAnd<float>>(OrAnd<float> *p, OrAnd<float> x) {
+    if (x.v != 0.0f) atomicOr(reinterpret_cast<unsigned int *>(p), __float_as_uint(1.0f));
+}
+template <> __device__ __forceinline__ void atomic_add_v<OrAnd<double>>(OrAnd<double> *p, OrAnd<double> x) {
+    if (x.v != 0.0) atomicOr(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double_as_longlong(1.0));
+}
+template <> __device__ __forceinline__ void atomic_add_v<OrAnd<int64_t>>(OrAnd<int64_t> *p, OrAnd<int64_t> x) {
+    if (x.v != 0) atomicOr(reinterpret_cast<unsigned long long *>(p), 1ull);
+}
+
 template <class T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(SPG_FULL, v, o);
@@ -145,3 +192,20 @@ __device__ __forceinline__ spg::MinPlus<double> __shfl_xor_sync(unsigned mask, s
                                                                 int lane_mask, int width = 32) {
     return spg::MinPlus<double>::raw(__shfl_xor_sync(mask, x.v, lane_mask, width));
 }
+// Loads and shuffles of or-and values (the stored bits), as for min-plus.
+#define SPG_ORAND_IO(T)                                                                           \
+    __device__ __forceinline__ spg::OrAnd<T> __ldg(const spg::OrAnd<T> *p) {                     \
+        return spg::OrAnd<T>::raw(__ldg(reinterpret_cast<const T *>(p)));                         \
+    }                                                                                             \
+    __device__ __forceinline__ spg::OrAnd<T> __shfl_sync(unsigned mask, spg::OrAnd<T> x, int src, \
+                                                         int width = 32) {                        \
+        return spg::OrAnd<T>::raw(__shfl_sync(mask, x.v, src, width));                            \
+    }                                                                                             \
+    __device__ __forceinline__ spg::OrAnd<T> __shfl_xor_sync(unsigned mask, spg::OrAnd<T> x,      \
+                                                             int lane_mask, int width = 32) {     \
+        return spg::OrAnd<T>::raw(__shfl_xor_sync(mask, x.v, lane_mask, width));                  \
+    }
+SPG_ORAND_IO(float)
+SPG_ORAND_IO(double)
+SPG_ORAND_IO(int64_t)
+#undef SPG_ORAND_IO

@@ -1025,20 +1025,20 @@ template <class I, class V> struct Engine : EngineBase {
     // The smallest value of type V that is >= thr (so that "v >= it" in V is
     // exactly "v >= thr" in double).
     static V typed_threshold(double thr) {
-        if constexpr (std::is_same<V, float>::value || std::is_same<V, MinPlus<float>>::value) {
-            float t = (float)thr;
+        using S = typename Storage<V>::type;
+        S t;
+        if constexpr (std::is_same<S, float>::value) {
+            t = (float)thr;
             if (std::isfinite(thr) && (double)t < thr) t = std::nextafterf(t, INFINITY);
-            if constexpr (std::is_same<V, float>::value) return t;
-            else return V::raw(t);
-        } else if constexpr (std::is_same<V, double>::value) {
-            return thr;
-        } else if constexpr (std::is_same<V, MinPlus<double>>::value) {
-            return V::raw(thr);
+        } else if constexpr (std::is_same<S, double>::value) {
+            t = thr;
         } else {
-            if (thr <= -9.2233720368547758e18) return INT64_MIN;
-            if (thr > 9.2233720368547748e18) return INT64_MAX;
-            return (int64_t)std::ceil(thr);
+            if (thr <= -9.2233720368547758e18) t = INT64_MIN;
+            else if (thr > 9.2233720368547748e18) t = INT64_MAX;
+            else t = (int64_t)std::ceil(thr);
         }
+        if constexpr (std::is_same<V, S>::value) return t;
+        else return V::raw(t);
     }
 
     // prune workspace bytes per column (PruneWs: keep, sel, key, quota 8 B, row
@@ -1156,7 +1156,7 @@ template <class I, class V> struct Engine : EngineBase {
             set_error("backward needs floating-point values");
             return SPGEMM_ERR_INVALID;
         }
-        if (IsMinPlus<V>::v) {
+        if (IsMinPlus<V>::v || IsOrAnd<V>::v) {
             set_error("backward is defined for the plus-times semiring only");
             return SPGEMM_ERR_INVALID;
         }

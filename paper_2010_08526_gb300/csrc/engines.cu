@@ -32,11 +32,23 @@ EngineBase *make_engine_i32_mpf32();
 EngineBase *make_engine_i32_mpf64();
 EngineBase *make_engine_i64_mpf32();
 EngineBase *make_engine_i64_mpf64();
+EngineBase *make_engine_i32_oaf32();
+EngineBase *make_engine_i32_oaf64();
+EngineBase *make_engine_i32_oai64();
+EngineBase *make_engine_i64_oaf32();
+EngineBase *make_engine_i64_oaf64();
+EngineBase *make_engine_i64_oai64();
 
 EngineBase *make_engine(int idx64, int vtype, int semiring) {
     if (semiring == SPGEMM_MIN_PLUS) {   // float values only (checked at plan time)
         if (vtype == SPGEMM_F32) return idx64 ? make_engine_i64_mpf32() : make_engine_i32_mpf32();
         if (vtype == SPGEMM_F64) return idx64 ? make_engine_i64_mpf64() : make_engine_i32_mpf64();
+        return nullptr;
+    }
+    if (semiring == SPGEMM_OR_AND) {     // any value type
+        if (vtype == SPGEMM_F32) return idx64 ? make_engine_i64_oaf32() : make_engine_i32_oaf32();
+        if (vtype == SPGEMM_F64) return idx64 ? make_engine_i64_oaf64() : make_engine_i32_oaf64();
+        if (vtype == SPGEMM_INT64) return idx64 ? make_engine_i64_oai64() : make_engine_i32_oai64();
         return nullptr;
     }
 #define MK(I, V) make_engine_##I##_##V()

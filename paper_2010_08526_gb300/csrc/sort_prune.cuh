@@ -33,9 +33,11 @@ __device__ __forceinline__ uint64_t value_key(double v) {
 }
 __device__ __forceinline__ uint64_t value_key(int64_t v) { return (uint64_t)v ^ 0x8000000000000000ull; }
 template <class F> __device__ __forceinline__ uint64_t value_key(MinPlus<F> v) { return value_key(v.v); }
+template <class T> __device__ __forceinline__ uint64_t value_key(OrAnd<T> v) { return value_key(v.v); }
 template <class V> struct KeyBits { static constexpr int v = 64; };
 template <> struct KeyBits<float> { static constexpr int v = 32; };
 template <> struct KeyBits<MinPlus<float>> { static constexpr int v = 32; };
+template <> struct KeyBits<OrAnd<float>> { static constexpr int v = 32; };
 
 // ---- sort ------------------------------------------------------------------
 // One warp per column of at most 32 entries: bitonic network over the lanes.
