@@ -384,6 +384,9 @@ def run_gpu(args):
         extras["min_plus"] = bench_step(spg, torch, args, A, dev, semiring="min_plus",
                                         note="the same product over the min-plus semiring")
         extras["min_plus"].pop("_counts")
+        extras["or_and"] = bench_step(spg, torch, args, A, dev, semiring="or_and",
+                                      note="the same product over the Boolean or-and semiring")
+        extras["or_and"].pop("_counts")
         extras["protein_2M"] = bench_protein(spg, torch, args, dev)
         extras["kmerge"] = bench_kmerge(spg, torch, args, A, dev)
 
