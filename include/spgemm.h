@@ -394,8 +394,10 @@ typedef struct spgemm_multi_s spgemm_multi;
  * rows stay local to each problem), with an int64 colptr over all
  * sum_i B_i.ncols columns. The arena is sized from the flop count
  * (nnz(C_i) <= flops_i), so the whole pipeline needs no host synchronisation
- * and can be captured in a CUDA graph. Errors: SPGEMM_ERR_INVALID, SPGEMM_ERR_OOM,
- * SPGEMM_ERR_CUDA.
+ * and can be captured in a CUDA graph. Of opts only the tuning applies:
+ * kstages > 1, a semiring other than plus-times, sort_output and prune are
+ * refused with SPGEMM_ERR_INVALID. Errors: SPGEMM_ERR_INVALID,
+ * SPGEMM_ERR_OOM, SPGEMM_ERR_CUDA.
  */
 spgemm_status spgemm_multi_create(int nprob, const spgemm_csc *As, const spgemm_csc *Bs,
                                   const spgemm_opts *opts, cudaStream_t stream,

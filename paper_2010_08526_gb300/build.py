@@ -26,7 +26,7 @@ SOURCES = [
     "inst_i32_mpf32.cu", "inst_i32_mpf64.cu", "inst_i64_mpf32.cu", "inst_i64_mpf64.cu",
     "inst_i32_oaf32.cu", "inst_i32_oaf64.cu", "inst_i32_oai64.cu",
     "inst_i64_oaf32.cu", "inst_i64_oaf64.cu", "inst_i64_oai64.cu",
-    "api.cu", "engines.cu", "util_kernels.cu", "batched.cu", "multi.cu", "noalloc.cu", "transpose.cu",
+    "api.cu", "engines.cu", "util_kernels.cu", "batched.cu", "noalloc.cu", "transpose.cu",
 ]
 
 

@@ -455,6 +455,11 @@ spgemm_status spgemm_multi_create(int nprob, const spgemm_csc *As, const spgemm_
     }
     if (total >= 0x7fffffffLL) { set_error("total columns must be < 2^31-1"); return SPGEMM_ERR_INVALID; }
     if (opts && opts->kstages > 1) { set_error("batched problems take no k-split"); return SPGEMM_ERR_INVALID; }
+    if (opts && (opts->semiring != SPGEMM_PLUS_TIMES || opts->sort_output || opts->prune)) {
+        set_error("batched problems run the plus-times product, unsorted and unpruned "
+                  "(semiring, sort_output and prune are plan options)");
+        return SPGEMM_ERR_INVALID;
+    }
     int dev = 0;
     cudaDeviceProp prop;
     cudaError_t e = cudaGetDevice(&dev);

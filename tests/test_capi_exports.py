@@ -85,3 +85,23 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, f"{cname}.{f}"
+
+
+def test_multi_create_refuses_plan_only_options_without_gpu():
+    """The multi-problem pass runs the plain plus-times product: a k-split, another
+    semiring, sorted output or a prune is refused before any device call
+    rather than ignored."""
+    from paper_2010_08526_gb300 import _capi as C
+    lib = C.load()
+    dummy = ctypes.c_void_p(64)      # never dereferenced: the checks come first
+    A = C.SpgemmCsc(4, 4, 0, dummy, None, None, 0, 0, 1)
+    B = C.SpgemmCsc(4, 4, 0, dummy, None, None, 0, 0, 1)
+    for field, value in (("kstages", 2), ("semiring", 1), ("semiring", 2), ("sort_output", 1), ("prune", 1)):
+        o = C.SpgemmOpts()
+        setattr(o, field, value)
+        h = ctypes.c_void_p()
+        st = lib.spgemm_multi_create(1, ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), None, ctypes.byref(h))
+        assert st == 1, (field, value)
+        assert not h.value
+        msg = lib.spgemm_last_error()
+        assert b"k-split" in msg or b"plus-times" in msg, msg
