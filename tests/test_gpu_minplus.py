@@ -62,14 +62,15 @@ def compare(C, ref, *, exact, scale=None, sorted_rows=False, label=""):
 
 
 @pytest.mark.parametrize("vt", [np.float64, np.float32])
-@pytest.mark.parametrize("case", ["light", "heavy", "ksplit", "sorted"])
+@pytest.mark.parametrize("case", ["light", "heavy", "ksplit", "incremental", "sorted"])
 def test_minplus_exact_on_integer_weights(vt, case):
     kw = {}
     A = graph(4000, 4000, 5, hubs=3, hub_deg=1600, base=6, value_dtype=vt)
-    if case in ("heavy", "ksplit", "sorted"):
+    if case in ("heavy", "ksplit", "incremental", "sorted"):
         kw["tuning"] = spg.Tuning(hash_max_cap=256, panel_rows=1024)
-    if case == "ksplit":
-        kw["kstages"] = 3
+    if case in ("ksplit", "incremental"):
+        kw["kstages"] = 3 if case == "ksplit" else 4
+        kw["merge"] = "end" if case == "ksplit" else "incremental"
     if case == "sorted":
         kw["sort_output"] = True
     Ad = to_dev(A)

@@ -115,6 +115,35 @@ def test_orand_run_batched_streams_the_product():
     assert np.array_equal(np.asarray(g.vals, np.float64), ref.vals)
 
 
+@pytest.mark.parametrize("k", [3, 50])
+def test_orand_sorted_topk_stream(k):
+    """Sorted output with a top-k prune in the batch loop: among equal values
+    (every kept value is 1) the smaller rows win, as after sorting; k = 3 and
+    50 reach the warp and block sorts after the prune. Equal to the oracle's
+    prune of the whole sorted or-and product."""
+    A = graph(3000, 3000, 13, hubs=2, hub_deg=1200, base=6, value_dtype=np.float32)
+    Ad = to_dev(A)
+    full = oracle.spgemm(A, A, semiring="or_and")
+    ref = oracle.prune(full, 0.5, k)          # true entries only, then the first k rows
+    tun = spg.Tuning(hash_max_cap=256, panel_rows=1024)
+    budget = A.bytes() * 3 + (2 << 20) + full.nnz * 8
+    plan = spg.Plan(Ad, Ad, budget=budget, semiring="or_and", sort_output=True, prune=(0.5, k), tuning=tun,
+                    host_slot_bytes=1 << 15, host_slots=2)
+    info = plan.symbolic()
+    assert info["heavy_columns"] > 0
+    pieces = []
+    spg.run_batched(plan, lambda b, c0, c1, arrs: pieces.append((c0, c1) + tuple(x.copy() for x in arrs)) or 0)
+    plan.close()
+    colptr = [0]
+    for c0, c1, cp, ri, va in pieces:
+        colptr.extend((cp[1:] + colptr[-1]).tolist())
+    got_rows = np.concatenate([p[3] for p in pieces]).astype(np.int64)
+    got_vals = np.concatenate([p[4] for p in pieces]).astype(np.float64)
+    assert np.array_equal(np.array(colptr, np.int64), ref.colptr)
+    assert np.array_equal(got_rows, ref.rowidx)                  # sorted, smallest rows kept
+    assert np.all(got_vals == 1.0) and np.array_equal(got_vals, ref.vals)
+
+
 def test_orand_backward_refused():
     A = graph(500, 500, 3, hubs=1, hub_deg=100)
     Ad = to_dev(A)

@@ -263,14 +263,15 @@ def test_incremental_merge_equals_unsplit(s):
     assert info["stage_buffer_nnz"] == max(d[1:]) + (2 if s > 2 else 1) * max(runs)
 
 
-@pytest.mark.parametrize("vt", [np.float32, np.int64])
-def test_incremental_heavy_dense_merge(vt):
+@pytest.mark.parametrize("vt,it", [(np.float32, np.int32), (np.int64, np.int32), (np.float64, np.int64)])
+def test_incremental_heavy_dense_merge(vt, it):
     """Heavy columns: the stage partials and the running sums are grouped by
     the heavy items' panel ranges; dense-panel and hash-range merge items."""
     dist = "normal" if vt != np.int64 else "ones"
-    A = skewed(5000, 5000, 71, hubs=4, hub_deg=2500, base=6, value_dtype=vt, dist=dist)
+    A = skewed(5000, 5000, 71, hubs=4, hub_deg=2500, base=6, index_dtype=it, value_dtype=vt, dist=dist)
     tun = spg.Tuning(hash_max_cap=256, panel_rows=1024)
-    info = check_product(A, A, f"incremental heavy {vt.__name__}", kstages=4, tuning=tun, merge="incremental")
+    info = check_product(A, A, f"incremental heavy {vt.__name__} {it.__name__}", kstages=4, tuning=tun,
+                         merge="incremental")
     assert info["heavy_columns"] > 0
 
 
