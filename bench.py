@@ -545,6 +545,12 @@ def bench_protein(spg, torch, args, dev):
     achieved = model / (num_ms / 1e3) / 1e9 if num_ms else 0.0
     r["roofline_numeric"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "algorithmic_bytes": model, "numeric_ms": num_ms}
+    # the hybrid accumulator on the same product: CTA-tier columns whose
+    # products fit their table are sorted by row instead of hashed
+    h = bench_step(spg, torch, args, A, dev, tuning=spg.Tuning(hybrid_sort=True),
+                   note="hybrid accumulator (sort-based for low-cf CTA-tier columns)")
+    h.pop("_counts")
+    r["hybrid_sort"] = {k: h[k] for k in ("value", "unit", "ms_per_step", "phase_ms_per_step", "note")}
     return r
 
 

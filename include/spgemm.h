@@ -115,6 +115,11 @@ typedef struct {
  *                  longer ones by a whole warp (1..64).
  *   huge_seg       segments longer than this are walked by the whole CTA.
  *   block_tier_threads  threads per CTA of the hash tiers (128..1024).
+ *   hybrid_sort    1: a column of the CTA hash tiers whose products fit its
+ *                  table (at most 2x its distinct rows, i.e. a low compression
+ *                  factor) is accumulated by sorting its products by row and
+ *                  summing equal rows instead of hashing them (a hybrid
+ *                  accumulator chosen per column); 0: hash only.
  */
 typedef struct {
     int hash_max_cap;
@@ -122,7 +127,8 @@ typedef struct {
     int short_seg;
     int huge_seg;
     int block_tier_threads;
-    int reserved[3];
+    int hybrid_sort;
+    int reserved[2];
 } spgemm_tuning;
 
 typedef struct {

@@ -90,12 +90,14 @@ class Tuning:
     short_seg: int = 0
     huge_seg: int = 0
     block_tier_threads: int = 0
+    hybrid_sort: bool = False
 
     def struct(self) -> C.SpgemmTuning:
         t = C.SpgemmTuning()
         t.hash_max_cap, t.panel_rows = self.hash_max_cap, self.panel_rows
         t.short_seg, t.huge_seg = self.short_seg, self.huge_seg
         t.block_tier_threads = self.block_tier_threads
+        t.hybrid_sort = int(bool(self.hybrid_sort))
         return t
 
 

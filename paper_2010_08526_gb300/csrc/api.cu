@@ -158,6 +158,7 @@ spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B, const
         if (tu->short_seg) ps.tun.short_seg = tu->short_seg;
         if (tu->huge_seg) ps.tun.huge_seg = tu->huge_seg;
         if (tu->block_tier_threads) ps.tun.block_threads = tu->block_tier_threads;
+        ps.tun.hybrid_sort = tu->hybrid_sort ? 1 : 0;
     }
     {
         bool ok = false;

@@ -146,6 +146,29 @@ template <> __device__ __forceinline__ void atomic_add_v<OrAnd<int64_t>>(OrAnd<i
     if (x.v != 0) atomicOr(reinterpret_cast<unsigned long long *>(p), 1ull);
 }
 
+// The semiring's sum of two values, for a sequential run (the sort-based
+// accumulator): + for plus-times (int64 wrapping), min for min-plus with NaN
+// operands skipped, OR for or-and. The same rules as atomic_add_v.
+template <class V> __device__ __forceinline__ V add_v(V a, V b) { return a + b; }
+template <> __device__ __forceinline__ int64_t add_v<int64_t>(int64_t a, int64_t b) {
+    return static_cast<int64_t>(static_cast<uint64_t>(a) + static_cast<uint64_t>(b));
+}
+template <> __device__ __forceinline__ MinPlus<float> add_v<MinPlus<float>>(MinPlus<float> a, MinPlus<float> b) {
+    return (b.v != b.v || !(b.v < a.v)) ? a : b;
+}
+template <> __device__ __forceinline__ MinPlus<double> add_v<MinPlus<double>>(MinPlus<double> a, MinPlus<double> b) {
+    return (b.v != b.v || !(b.v < a.v)) ? a : b;
+}
+template <> __device__ __forceinline__ OrAnd<float> add_v<OrAnd<float>>(OrAnd<float> a, OrAnd<float> b) {
+    return b.v != 0.0f ? OrAnd<float>(1) : a;
+}
+template <> __device__ __forceinline__ OrAnd<double> add_v<OrAnd<double>>(OrAnd<double> a, OrAnd<double> b) {
+    return b.v != 0.0 ? OrAnd<double>(1) : a;
+}
+template <> __device__ __forceinline__ OrAnd<int64_t> add_v<OrAnd<int64_t>>(OrAnd<int64_t> a, OrAnd<int64_t> b) {
+    return b.v != 0 ? OrAnd<int64_t>(1) : a;
+}
+
 template <class T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(SPG_FULL, v, o);

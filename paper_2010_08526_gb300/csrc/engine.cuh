@@ -49,6 +49,7 @@ struct Ctx {
     PhaseTimer *tm = nullptr;   // optional phase timing and launch counting
     int ph_hash = kPhNumHash, ph_dense = kPhNumDense;
     bool stage_items = false;   // heavy items take their counts from pcnt_in
+    const int64_t *f = nullptr; // flops per column of the full product (hybrid accumulator)
     int tbegin(int phase, cudaStream_t st) const { return tm ? tm->begin(phase, st) : -1; }
     void tend(int idx, cudaStream_t st) const { if (tm) tm->end(idx, st); }
     void launched(int n = 1) const { if (tm) tm->launches += n; }
@@ -61,6 +62,7 @@ inline Ctx make_ctx(PlanState &ps) {
     c.hist = ps.hist.as<int32_t>(); c.cursor = ps.cursor.as<int32_t>();
     c.h_small = ps.h_small.as<int32_t>();
     c.P = ps.P; c.Q = ps.Q; c.Rs = ps.Rs;
+    c.f = ps.f.as<int64_t>();
     return c;
 }
 
@@ -71,6 +73,8 @@ inline TierCommon common_of(const Ctx &c) {
     t.err = c.err;
     t.hash_cap_max = c.tun.hash_cap_max;
     t.P = c.P; t.log2R = c.tun.log2R; t.Rs = c.Rs; t.Q = c.Q;
+    t.flops = c.f;
+    t.hybrid_sort = c.tun.hybrid_sort;
     return t;
 }
 

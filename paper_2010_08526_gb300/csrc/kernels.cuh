@@ -84,6 +84,8 @@ struct TierCommon {
     int64_t c_lo, c_hi;      // global column range (dense items)
     int item_counts_from_pcnt; // heavy items: take count / offset from pcnt_in (a k-stage)
     int range_cap;             // heavy hash items: at most this many output rows
+    const int64_t *flops;      // flops per global column (hybrid accumulator), or null
+    int hybrid_sort;           // CTA tiers: sort-accumulate columns with flops <= table size
 };
 
 template <class I, class V> struct GemmArgs {
@@ -921,6 +923,100 @@ __global__ void __launch_bounds__(256) k_num_warp(typename Src::Args sa, TierCom
     }
 }
 
+// Bitonic sort of one segment of n <= CAP entries in shared memory (keys
+// padded with 0xffffffff to the next power of two). All threads call it.
+template <int CAP, class V>
+__device__ __forceinline__ void block_bitonic(uint32_t *sk, V *sv, int n) {
+    int np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    for (int i = n + threadIdx.x; i < np2; i += blockDim.x) { sk[i] = 0xffffffffu; sv[i] = V(0); }
+    __syncthreads();
+    for (int k = 2; k <= np2; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+                const int l = i ^ jj;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const uint32_t a = sk[i], b = sk[l];
+                    if (up ? a > b : a < b) {
+                        sk[i] = b; sk[l] = a;
+                        const V t = sv[i]; sv[i] = sv[l]; sv[l] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Sort-based accumulation of one column, the hybrid accumulator's other
+// half: with few products per distinct row (low compression), appending the
+// products and sorting them by row can replace the hash. The products are
+// appended to keys / vals (T slots; the caller checked flops <= T) with one
+// shared counter bump per warp window, sorted by row (block bitonic), and
+// each run of equal rows is summed in sorted order with the semiring's sum.
+// The column is written in ascending row order. sh.pos is 0 on entry and on
+// return; all threads call it; it ends with a barrier.
+template <class Src, int T>
+__device__ __forceinline__ void num_block_sorted(const Src &src, const TierCommon &c, uint32_t *keys,
+                                                 typename Src::Val *vals, BlockShared<typename Src::Val> &sh,
+                                                 int64_t out0, int64_t want, typename Src::Idx *out_rows,
+                                                 typename Src::Val *out_vals) {
+    using V = typename Src::Val;
+    using I = typename Src::Idx;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    auto emit = load_apply(
+        [&](int64_t q, V bv, int64_t) { return RowVal<V>{src.row(q), src.val(q, bv)}; },
+        [&](const RowVal<V> &e, bool valid) {
+            const bool ok = valid && e.r != kEmpty;
+            const unsigned bal = __ballot_sync(SPG_FULL, ok);
+            int base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&sh.pos, __popc(bal));
+            base = __shfl_sync(SPG_FULL, base, 0);
+            if (ok) {
+                const int at = base + __popc(bal & below);
+                if (at < T) { keys[at] = e.r; vals[at] = e.x; }
+                else atomicOr(c.err, kErrCount);
+            }
+        });
+    block_walk<kWalkBatch>(src, emit, c.short_seg, c.huge_seg, sh);
+    const int n = sh.pos < T ? sh.pos : T;
+    block_bitonic<T>(keys, vals, n);
+    // runs of equal rows: a run's first entry sums it and writes it at the
+    // number of runs before it
+    int base = 0;
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const bool head = i < n && (i == 0 || keys[i] != keys[i - 1]);
+        const unsigned bal = __ballot_sync(SPG_FULL, head);
+        if (lane == 0) sh.red[warp] = __popc(bal);
+        __syncthreads();
+        int woff = 0, tot = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int x = sh.red[w];
+            woff += w < warp ? x : 0;
+            tot += x;
+        }
+        if (head) {
+            V acc = V(0);
+            for (int k = i; k < n && keys[k] == keys[i]; ++k) acc = add_v(acc, vals[k]);
+            const int64_t r = base + woff + __popc(bal & below);
+            if (r < want) {
+                out_rows[out0 + r] = (I)keys[i];
+                out_vals[out0 + r] = acc;
+            }
+        }
+        base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (base != want) atomicOr(c.err, kErrCount);
+        sh.pos = 0;
+    }
+    __syncthreads();
+}
+
 template <class Src, int T>
 __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::Idx *out_rows,
                             typename Src::Val *out_vals) {
@@ -938,6 +1034,12 @@ __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::I
         const int64_t g = c.list[it];
         Src src;
         src.open(sa, g);
+        const int64_t out0 = c.colptr[g] - c.out_base;
+        const int64_t want = c.colptr[g + 1] - c.colptr[g];
+        if (c.hybrid_sort && c.flops && c.flops[g] <= T) {   // the same branch for the whole CTA
+            num_block_sorted<Src, T>(src, c, keys, vals, sh, out0, want, out_rows, out_vals);
+            continue;
+        }
         for (int s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = kEmpty; vals[s] = V(0); }
         __syncthreads();
         auto emit = load_apply(
@@ -949,8 +1051,6 @@ __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::I
                 if (h >= 0) atomic_add_v(&vals[h], e.x);
             });
         block_walk<kWalkBatch>(src, emit, c.short_seg, c.huge_seg, sh);
-        const int64_t out0 = c.colptr[g] - c.out_base;
-        const int64_t want = c.colptr[g + 1] - c.colptr[g];
         for (int s0 = 0; s0 < T; s0 += blockDim.x) {
             const int s = s0 + threadIdx.x;
             const uint32_t key = s < T ? keys[s] : kEmpty;

@@ -75,6 +75,7 @@ struct Tuning {
     int short_seg = 1;
     int huge_seg = 4096;
     int block_threads = 0;   // 0: per-tier default
+    int hybrid_sort = 0;     // CTA tiers: sort-accumulate columns whose products fit the table
 };
 
 struct Batch {

@@ -68,32 +68,6 @@ __global__ void __launch_bounds__(256) k_sort_warp(const int64_t *colptr, int64_
     }
 }
 
-// Bitonic sort of one segment of n <= CAP entries in shared memory (keys
-// padded with 0xffffffff to the next power of two). All threads call it.
-template <int CAP, class V>
-__device__ __forceinline__ void block_bitonic(uint32_t *sk, V *sv, int n) {
-    int np2 = 1;
-    while (np2 < n) np2 <<= 1;
-    for (int i = n + threadIdx.x; i < np2; i += blockDim.x) { sk[i] = 0xffffffffu; sv[i] = V(0); }
-    __syncthreads();
-    for (int k = 2; k <= np2; k <<= 1) {
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-                const int l = i ^ jj;
-                if (l > i) {
-                    const bool up = (i & k) == 0;
-                    const uint32_t a = sk[i], b = sk[l];
-                    if (up ? a > b : a < b) {
-                        sk[i] = b; sk[l] = a;
-                        const V t = sv[i]; sv[i] = sv[l]; sv[l] = t;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
 // One CTA per light column with 32 < n <= CAP (and n <= cap_max, i.e. not a
 // heavy column), columns [c0, c1).
 template <class I, class V, int CAP>
