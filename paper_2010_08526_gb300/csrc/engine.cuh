@@ -268,9 +268,12 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(ioff.ensure(sizeof(int64_t) * (nheavy + 1)));
         SPG_CK(scan_part.ensure(sizeof(int64_t) * scan_partials_len(std::max<int64_t>(n, nheavy) + 1)));
         const int R = 1 << cx.tun.log2R;
-        const int dmin = std::max(1, R / 8);
-        const unsigned nb = (unsigned)((nheavy + 255) / 256);
+        // a panel with at least R/8 output rows is a dense item; the rest are
+        // grouped into hash items of at most range_cap rows, so a lone panel
+        // below the dense threshold must fit one (dense_min - 1 <= range_cap)
         const int rcap = range_cap(cx);
+        const int dmin = std::max(1, std::min(R / 8, rcap));
+        const unsigned nb = (unsigned)((nheavy + 255) / 256);
         k_heavy_items<<<nb, 256, 0, st>>>(sym_list, sym_off, sel, cx.tun.hash_cap_max, 0, n, pcnt, cx.P,
                                           dmin, rcap, 0, icnt.as<int64_t>(), nullptr, nullptr);
         SPG_CK(exclusive_scan_i64(icnt.as<int64_t>(), nheavy, ioff.as<int64_t>(),
