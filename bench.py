@@ -168,14 +168,32 @@ def cpu_oracle_sample(A, f, target_flops, threads=None):
     cs = np.cumsum(f[c0:])
     c1 = c0 + int(np.searchsorted(cs, target_flops)) + 1
     c1 = min(c1, A.ncols)
-    Bs = column_slice(A, c0, c1)
     fl = int(f[c0:c1].sum())
     cores = oracle.num_threads()
-    t0 = time.perf_counter()
-    C = oracle.spgemm(A, Bs)
-    dt = time.perf_counter() - t0
+    # the range in pieces of at most ~1.5e9 multiplies, each product freed
+    # before the next, so host memory holds one piece's output (~10 GB), not
+    # the whole sample's; only the oracle calls are timed
+    piece = 1.5e9
+    cuts = [c0]
+    acc = 0
+    for j in range(c0, c1):
+        acc += int(f[j])
+        if acc >= piece and j + 1 < c1:
+            cuts.append(j + 1)
+            acc = 0
+    cuts.append(c1)
+    dt = 0.0
+    nnz = 0
+    for a, b in zip(cuts, cuts[1:]):
+        Bs = column_slice(A, a, b)
+        t0 = time.perf_counter()
+        C = oracle.spgemm(A, Bs)
+        dt += time.perf_counter() - t0
+        nnz += C.nnz
+        del C, Bs
     desc = (f"columns [{c0}, {c1}) of the workload ({c1 - c0} columns, {fl:.3e} multiplies, "
-            f"nnz(C) {C.nnz}), oracle symbolic + numeric, float64 accumulation")
+            f"nnz(C) {nnz}, in {len(cuts) - 1} column pieces), oracle symbolic + numeric, "
+            f"float64 accumulation")
     return 2 * fl / dt / 1e9, desc, cores, dt
 
 
@@ -187,8 +205,11 @@ def run_reference(args):
     f = flops_host(A)
     vals = []
     desc = cores = None
+    # every step is a bounded sample: about 2 minutes of oracle work over the
+    # whole run (at ~1 GFLOP/s on 16 cores), and never more than --ref-flops
+    per_step = max(2e8, min(args.ref_flops, 6e10 / max(1, args.warmup + args.steps)))
     for i in range(args.warmup + args.steps):
-        v, desc, cores, _ = cpu_oracle_sample(A, f, args.ref_flops)
+        v, desc, cores, _ = cpu_oracle_sample(A, f, per_step)
         if i >= args.warmup:
             vals.append(v)
     v = float(np.mean(vals))
