@@ -105,3 +105,36 @@ def test_multi_create_refuses_plan_only_options_without_gpu():
         assert not h.value
         msg = lib.spgemm_last_error()
         assert b"k-split" in msg or b"plus-times" in msg, msg
+
+
+def test_plan_create_rejects_bad_options_without_gpu():
+    """Option checks run before any device call: an unknown merge mode or
+    semiring, and min-plus on int64 values, are refused."""
+    from paper_2010_08526_gb300 import _capi as C
+    lib = C.load()
+    dummy = ctypes.c_void_p(64)      # never dereferenced: the checks come first
+    f32 = C.SpgemmCsc(4, 4, 0, dummy, None, None, 0, 0, 1)
+    i64 = C.SpgemmCsc(4, 4, 0, dummy, None, None, 0, 0, 2)
+    cases = [(f32, "merge_mode", 7, b"merge_mode"), (f32, "semiring", 9, b"semiring"),
+             (i64, "semiring", 1, b"floating-point")]
+    for M, field, value, word in cases:
+        o = C.SpgemmOpts()
+        setattr(o, field, value)
+        h = ctypes.c_void_p()
+        st = lib.spgemm_plan_create(ctypes.byref(M), ctypes.byref(M), ctypes.byref(o), 0, None, ctypes.byref(h))
+        assert st == 1, (field, value)
+        assert not h.value
+        assert word in lib.spgemm_last_error(), lib.spgemm_last_error()
+
+
+def test_python_option_names():
+    import pytest
+    from paper_2010_08526_gb300 import core
+    o, _ = core._opts(semiring="or_and", merge="incremental", kstages=3)
+    assert (o.semiring, o.merge_mode, o.kstages) == (2, 1, 3)
+    with pytest.raises(ValueError):
+        core._opts(merge="later")
+    with pytest.raises(ValueError):
+        core._opts(semiring="max_times")
+    assert core.Tuning(hybrid_sort=True).struct().hybrid_sort == 1
+    assert core.Tuning().struct().hybrid_sort == 0
