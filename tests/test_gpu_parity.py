@@ -553,3 +553,41 @@ def test_multi_path_counting_exact():
             assert_matches(got, ref, exact=True, label="multi")
             col += p.ncols
         M.close()
+
+
+# ------------------------------------------------------ every output slot written
+
+@pytest.mark.parametrize("kst,sort_output", [(1, False), (3, False), (1, True)])
+def test_poisoned_outputs_are_fully_written(kst, sort_output):
+    """Output buffers filled with a poison (row -7, value NaN) before the
+    numeric: after every batch no poison is left, and the result is the
+    oracle's. Catches slots no kernel writes, which fresh or reused memory
+    could otherwise hide. Heavy columns included (small tables and panels)."""
+    A = skewed(4000, 4000, 91, hubs=3, hub_deg=1500, base=6)
+    Ad = to_dev(A)
+    ref, ab = oracle.spgemm(A, A, with_absterm=True)
+    tun = spg.Tuning(hash_max_cap=256, panel_rows=1024)
+    plan = spg.Plan(Ad, Ad, kstages=kst, tuning=tun, sort_output=sort_output,
+                    budget=A.bytes() * 2 + (2 << 20) + ref.nnz * 12 * kst)
+    info = plan.symbolic()
+    assert info["nbatches"] >= 2 and info["heavy_columns"] > 0
+    nnz = int(info["nnz_c"])
+    rows = torch.full((nnz,), -7, dtype=torch.int32, device="cuda")
+    vals = torch.full((nnz,), float("nan"), dtype=torch.float64, device="cuda")
+    scratch = torch.full((int(info["max_batch_cols"]) + 1,), -7, dtype=torch.int64, device="cuda")
+    off = 0
+    for t in range(plan.nbatches):
+        c0, c1, bn = plan.batch(t)
+        plan.numeric_into(t, scratch[: c1 - c0 + 1], rows[off:off + bn], vals[off:off + bn])
+        assert int(scratch[c1 - c0].item()) == bn        # the batch colptr is written too
+        off += bn
+    torch.cuda.synchronize()
+    counts = plan.column_counts().cpu().numpy()
+    plan.close()
+    r = rows.cpu().numpy()
+    v = vals.cpu().numpy()
+    assert off == nnz and (r >= 0).all() and not np.isnan(v).any()
+    got = CSC(A.nrows, A.ncols, np.concatenate([[0], np.cumsum(counts)]).astype(np.int64), r, v)
+    if sort_output:
+        assert np.array_equal(got.rowidx.astype(np.int64), ref.rowidx)
+    assert_matches(got, ref, ab, label=f"poisoned s={kst} sorted={sort_output}")
