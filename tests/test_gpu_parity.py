@@ -167,6 +167,33 @@ def test_edge_cases():
     check_product(Ab, Bb, "large rows")
 
 
+@pytest.mark.parametrize("kst,merge", [(2, "end"), (3, "incremental"), (5, "incremental"), (2, "incremental")])
+def test_edge_cases_with_stages(kst, merge):
+    """The degenerate inputs through the k-split, both merge modes: stages
+    with no entries, more stages than some columns have entries, and the
+    running sums' buffers at their smallest."""
+    Z = CSC(5, 4, np.zeros(5, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    B = CSC(4, 3, np.zeros(4, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    got, info = run(Z, B, kstages=kst, merge=merge)
+    assert info["nnz_c"] == 0 and got.nnz == 0 and got.ncols == 3
+    A1 = from_coo(1, 1, [0], [0], [3.0])
+    check_product(A1, A1, f"1x1 s={kst} {merge}", kstages=kst, merge=merge)
+    A = rand_csc(200, 200, 0.02, 41)
+    I = from_coo(200, 200, np.arange(200), np.arange(200), np.ones(200))
+    check_product(A, I, f"A*I s={kst} {merge}", kstages=kst, merge=merge)
+    check_product(I, A, f"I*A s={kst} {merge}", kstages=kst, merge=merge)
+    # B with empty columns and a k smaller than the number of stages
+    Ak = rand_csc(300, 3, 0.5, 42)
+    Bk = from_coo(3, 6, [0, 2, 1], [0, 0, 4], [1.0, -2.0, 0.5])
+    check_product(Ak, Bk, f"k=3 s={kst} {merge}", kstages=kst, merge=merge)
+
+
+def test_hybrid_with_int64_indices():
+    """The sort-based accumulator with 64-bit indices (rows < 2^31 as keys)."""
+    A = W.er_exact(6000, 6000, 40, 17, index_dtype=np.int64)
+    check_product(A, A, "hybrid int64 indices", tuning=spg.Tuning(hybrid_sort=True))
+
+
 def test_row_order_invariance_on_gpu():
     A = W.config1(n=1024)
     A2 = shuffle_within_columns(A, 99)
