@@ -150,3 +150,30 @@ def test_minplus_dense_items_after_hash_items_on_one_cta():
     assert C.plan_info["heavy_columns"] > 1000
     ref = oracle.spgemm(A, B, semiring="min_plus")
     compare(C, ref, exact=True, label="min-plus dense after hash")
+
+
+@pytest.mark.parametrize("thr,k", [(float("-inf"), 5), (300.0, 0), (100.0, 40)])
+def test_minplus_sorted_prune_stream(thr, k):
+    """The batch loop's prune over min-plus values (the prune rule is the
+    same: values >= threshold, then the k largest, ties to the smaller row
+    once sorted). Integer weights keep every sum exact, so the streamed
+    selection equals the oracle's prune of the sorted product."""
+    A = graph(3000, 3000, 21, hubs=2, hub_deg=1200, base=6)
+    Ad = to_dev(A)
+    full = oracle.spgemm(A, A, semiring="min_plus")
+    ref = oracle.prune(full, thr, k)
+    budget = A.bytes() * 3 + (2 << 20) + full.nnz * 12
+    plan = spg.Plan(Ad, Ad, budget=budget, semiring="min_plus", sort_output=True, prune=(thr, k),
+                    tuning=spg.Tuning(hash_max_cap=256, panel_rows=1024), host_slot_bytes=1 << 15,
+                    host_slots=2)
+    assert plan.symbolic()["heavy_columns"] > 0
+    pieces = []
+    spg.run_batched(plan, lambda b, c0, c1, arrs: pieces.append((c0, c1) + tuple(x.copy() for x in arrs)) or 0)
+    plan.close()
+    colptr = [0]
+    for c0, c1, cp, ri, va in pieces:
+        colptr.extend((cp[1:] + colptr[-1]).tolist())
+    assert np.array_equal(np.array(colptr, np.int64), ref.colptr)
+    assert np.array_equal(np.concatenate([p[3] for p in pieces]).astype(np.int64), ref.rowidx)
+    assert np.array_equal(np.concatenate([p[4] for p in pieces]).astype(np.float64), ref.vals)
+    assert ref.nnz < full.nnz
