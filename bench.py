@@ -655,18 +655,22 @@ def bench_fwdbwd(spg, torch, args):
     A, B = W.config5()
     Ad, Bd = spg.Csc.from_host(A), spg.Csc.from_host(B)
     At, Bt = spg.Csc.from_host(transpose(A)), spg.Csc.from_host(transpose(B))
-    torch.manual_seed(0)
+    # G: N(0,1) values on C's pattern (seeded), the same for both paths
+    gen = torch.Generator(device=Ad.vals.device)
+    gen.manual_seed(W.config_seed(5))
+    nnz_c = spg.spgemm(Ad, Bd, ptr_dtype=torch.int32).nnz
+    gvals = torch.randn(nnz_c, generator=gen, device=Ad.vals.device, dtype=Ad.vals.dtype)
 
     def fused():
         a = Ad.vals.detach().clone().requires_grad_(True)
         b = Bd.vals.detach().clone().requires_grad_(True)
         c = spg.SpGEMMFn.apply(a, b, Ad, Bd)
-        c.backward(torch.ones_like(c))
+        c.backward(gvals)
         return a.grad, b.grad
 
     def plain():
         C = spg.spgemm(Ad, Bd, ptr_dtype=torch.int32)
-        G = spg.Csc(C.nrows, C.ncols, C.colptr, C.rowidx, torch.ones_like(C.vals))
+        G = spg.Csc(C.nrows, C.ncols, C.colptr, C.rowidx, gvals)
         gb = spg.spgemm(G, Bt)          # G * B^T  (m x k), masked to pattern(A) by the caller
         ag = spg.spgemm(At, G)          # A^T * G  (k x n), masked to pattern(B)
         return gb, ag

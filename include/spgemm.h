@@ -214,6 +214,23 @@ spgemm_status spgemm_plan_destroy(spgemm_plan *plan);
  * nnz(D_t(:, j)) whose sum is the unmerged memory of Eq. (1), and the batch
  * plan: the smallest number of contiguous column ranges whose outputs fit the
  * budget (Eq. (2), Sec. V-C). Synchronises the stream once (to read totals).
+ *
+ * The batch plan. With r = index bytes + value bytes, a batch over columns
+ * [c0, c1) needs these bytes (sums over the batch's columns j):
+ *   sum_j (r nnz(C(:,j)) + 8)                      the output and an int64 colptr
+ *   + r sum_j sum_t nnz(D_t(:,j))                  kstages = s > 1, merge at the end:
+ *                                                  every stage partial of the batch
+ *   + r (max_{t>=1} sum_j nnz(D_t(:,j))            s > 1, incremental merge: one stage
+ *        + m max_{u<=s-2} sum_j nnz(M_u(:,j)))     partial and m running sums (m = 2,
+ *                                                  1 when s = 2; M_u = the product over
+ *                                                  stages 0..u, M_0 = D_0)
+ *   + sum_j (r min(nnz(C(:,j)), topk) + 8 + 40)    opts.prune: the pruned copy, its
+ *                                                  colptr and 40 B of prune workspace
+ *                                                  per column (topk <= 0: nnz(C(:,j)))
+ * The cap of one batch (spgemm_plan_info.batch_cap_bytes) is (budget -
+ * r (nnz(A) + nnz(B)) - index bytes (ncols(A) + ncols(B) + 2) - plan
+ * workspace) / ring_depth. Starting at column 0, each range is extended while
+ * the next column still fits under the cap; b is the number of ranges.
  * Errors: SPGEMM_ERR_BUDGET (inputs alone exceed the budget, or one column's
  * output exceeds a batch), SPGEMM_ERR_CUDA, SPGEMM_ERR_OOM.
  */
@@ -333,12 +350,16 @@ spgemm_status spgemm_transpose(const spgemm_csc *in, spgemm_csc *out, cudaStream
  * It calls no cudaMalloc, cudaFree or other allocating routine: its work
  * buffers live in one 32 MiB device array that every GPU loading the library
  * keeps until exit, so it accepts at most about 1.1 million columns
- * (29 bytes per column plus a few KiB) and at most 64 parts, and every merged
- * column must hold at most 8192 distinct rows (the shared-memory hash tables);
- * larger inputs return SPGEMM_ERR_INVALID with the limit in the message. The
- * first call on each device looks up the array's address on that device, so
- * make it before any stream capture. All calls share the array (it keeps the
- * last call's contents): calls that overlap on the GPU race, so serialise them.
+ * (29 bytes per column plus a few KiB) and at most 64 parts, and for every
+ * column the number of entries summed over the parts, capped at nrows, must
+ * be at most 8192 (the tier is chosen from that bound before the rows are
+ * counted, and the largest shared-memory hash table holds 8192 rows; parts
+ * that share rows count each copy); larger inputs return SPGEMM_ERR_INVALID
+ * with the limit in the message. The first call on each device looks up the
+ * array's address on that device, so make it before any stream capture. Every
+ * call synchronises the stream once (to read the merged size). All calls on
+ * one device share that device's array (it keeps the last call's contents):
+ * calls that overlap on one GPU race, so serialise them.
  * Errors: as spgemm_merge, plus SPGEMM_ERR_INVALID for sizes beyond the array.
  */
 spgemm_status spgemm_merge_noalloc(const spgemm_csc *parts, int nparts, spgemm_csc *out,

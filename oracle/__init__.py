@@ -50,7 +50,7 @@ def _lib():
         lib.oracle_flops.argtypes = [P(_OCSC), P(_OCSC), i64, i64, vp]
         lib.oracle_symbolic.argtypes = [P(_OCSC), P(_OCSC), i64, i64, i64, i64, vp]
         lib.oracle_spgemm.argtypes = [P(_OCSC), P(_OCSC), ctypes.c_int, i64, i64, i64, i64,
-                                      vp, vp, vp, vp]
+                                      vp, vp, vp, vp, vp]
         lib.oracle_merge.argtypes = [P(_OCSC), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      vp, vp, vp]
         lib.oracle_backward.argtypes = [P(_OCSC), P(_OCSC), P(_OCSC), vp, vp]
@@ -135,7 +135,7 @@ def _sr_vtype(dtype, semiring: str) -> int:
 
 
 def spgemm(A: CSC, B: CSC, krange=None, cols=None, with_absterm: bool = False,
-           semiring: str = "plus_times"):
+           semiring: str = "plus_times", with_nterm: bool = False):
     """C(:, c0:c1) = A(:, K) B(K, c0:c1) by column Gustavson (Sec. II-C).
 
     semiring "min_plus": C(i, j) = min over k of A(i, k) + B(k, j) on the same
@@ -145,7 +145,10 @@ def spgemm(A: CSC, B: CSC, krange=None, cols=None, with_absterm: bool = False,
 
     Returns a CSC (int64 indices, float64 or int64 values, rows sorted) and,
     if asked, the per-entry rounding-error scale: sum |products| (plus-times)
-    or the largest |a| + |b| over the entry's candidates (min-plus).
+    or the largest |a| + |b| over the entry's candidates (min-plus); and, with
+    ``with_nterm``, the per-entry number of products n_ij that reach (i, j)
+    (the n of that entry's own summation error bound). The result is
+    C, then absterm if asked, then nterm if asked.
     """
     if A.ncols != B.nrows:
         raise ValueError("inner dimensions differ")
@@ -162,11 +165,18 @@ def spgemm(A: CSC, B: CSC, krange=None, cols=None, with_absterm: bool = False,
     rowidx = np.zeros(nnz, dtype=np.int64)
     vals = np.zeros(nnz, dtype=np.int64 if vt in (2, 5) else np.float64)
     absterm = np.zeros(nnz, dtype=np.float64) if (with_absterm and vt in (0, 3)) else None
+    nterm = np.zeros(nnz, dtype=np.int64) if with_nterm else None
     lib.oracle_spgemm(ctypes.byref(ha.s), ctypes.byref(hb.s), vt, k0, k1, c0, c1,
                       _ptr(colptr), _ptr(rowidx), _ptr(vals),
-                      _ptr(absterm) if absterm is not None else None)
+                      _ptr(absterm) if absterm is not None else None,
+                      _ptr(nterm) if nterm is not None else None)
     C = CSC(A.nrows, c1 - c0, colptr, rowidx, vals)
-    return (C, absterm) if with_absterm else C
+    out = (C,)
+    if with_absterm:
+        out += (absterm,)
+    if with_nterm:
+        out += (nterm,)
+    return out if len(out) > 1 else C
 
 
 def merge(parts, semiring: str = "plus_times") -> CSC:
@@ -260,6 +270,28 @@ def plan_batches(w: np.ndarray, cap: int):
     if b < 0:
         return None
     return begin[: b + 1].copy()
+
+
+def plan_ranges(cost, n: int, cap: int):
+    """The same greedy cut for a batch cost that is not a sum over columns:
+    cost(c0, c1) = bytes a batch over columns [c0, c1) needs, non-decreasing
+    as the range grows. Starting at column 0, each range is extended while
+    the next column still fits under ``cap`` (Sec. V-C: the smallest b whose
+    batches fit). Returns the range starts plus n, or None when a single
+    column alone exceeds ``cap``. Plain Python; for the small plans of tests."""
+    begin = [0]
+    c = 0
+    if n == 0:
+        return np.array([0, 0], dtype=np.int64)
+    while c < n:
+        if cost(c, c + 1) > cap:
+            return None
+        x = c + 1
+        while x < n and cost(c, x + 1) <= cap:
+            x += 1
+        begin.append(x)
+        c = x
+    return np.array(begin, dtype=np.int64)
 
 
 def canonical(C: CSC) -> CSC:

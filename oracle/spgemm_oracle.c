@@ -114,11 +114,14 @@ void oracle_symbolic(const ocsc *A, const ocsc *B, int64_t k0, int64_t k1,
  * The caller supplies colptr_out (c1-c0+1 entries, from oracle_symbolic's
  * counts) and arrays of that many entries. absterm_out (may be NULL; float
  * only) receives sum |A(i,k) B(k,j)| per output entry, the scale of the
- * rounding error any reordering of the sum may have.
+ * rounding error any reordering of the sum may have. nterm_out (may be NULL)
+ * receives, per output entry, the number of products A(i,k) B(k,j) that reach
+ * it: the n of the summation error bound of that entry alone.
  */
 void oracle_spgemm(const ocsc *A, const ocsc *B, int vtype, int64_t k0, int64_t k1,
                    int64_t c0, int64_t c1, const int64_t *colptr_out,
-                   int64_t *rowidx_out, void *vals_out, double *absterm_out) {
+                   int64_t *rowidx_out, void *vals_out, double *absterm_out,
+                   int64_t *nterm_out) {
 #pragma omp parallel
     {
         int64_t m = A->nrows > 0 ? A->nrows : 1;
@@ -126,6 +129,7 @@ void oracle_spgemm(const ocsc *A, const ocsc *B, int vtype, int64_t k0, int64_t 
         double *spa = (double *)malloc(sizeof(double) * (size_t)m);
         double *spa_abs = (double *)malloc(sizeof(double) * (size_t)m);
         uint64_t *spa_i = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)m);
+        int64_t *spa_n = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
         for (int64_t i = 0; i < A->nrows; ++i) mark[i] = -1;
 #pragma omp for schedule(dynamic, 64)
         for (int64_t j = c0; j < c1; ++j) {
@@ -140,8 +144,9 @@ void oracle_spgemm(const ocsc *A, const ocsc *B, int vtype, int64_t k0, int64_t 
                         mark[i] = j;
                         rowidx_out[base + len++] = i;
                         spa[i] = vtype == 3 ? INFINITY : 0.0;   /* the (+) identity */
-                        spa_abs[i] = 0.0; spa_i[i] = 0;
+                        spa_abs[i] = 0.0; spa_i[i] = 0; spa_n[i] = 0;
                     }
+                    ++spa_n[i];
                     if (vtype == 2) {
                         uint64_t a = (uint64_t)((const int64_t *)A->vals)[q];
                         uint64_t b = (uint64_t)((const int64_t *)B->vals)[p];
@@ -173,9 +178,10 @@ void oracle_spgemm(const ocsc *A, const ocsc *B, int vtype, int64_t k0, int64_t 
                     ((double *)vals_out)[base + t] = spa[i];
                     if (absterm_out) absterm_out[base + t] = spa_abs[i];
                 }
+                if (nterm_out) nterm_out[base + t] = spa_n[i];
             }
         }
-        free(mark); free(spa); free(spa_abs); free(spa_i);
+        free(mark); free(spa); free(spa_abs); free(spa_i); free(spa_n);
     }
 }
 

@@ -75,8 +75,8 @@ static spgemm_status check_csc(const spgemm_csc *M, const char *name, bool input
     if (input && M->ptr_type != M->idx_type) {
         set_error(std::string(name) + ": input ptr_type must equal idx_type"); return SPGEMM_ERR_INVALID;
     }
-    if (M->nrows >= 0x7fffffffLL) {
-        set_error(std::string(name) + ": nrows must be < 2^31-1"); return SPGEMM_ERR_INVALID;
+    if (M->nrows > 0x7fffffffLL) {   // row indices <= 2^31 - 2: 0xffffffff stays the empty hash key
+        set_error(std::string(name) + ": nrows must be <= 2^31-1"); return SPGEMM_ERR_INVALID;
     }
     if (M->idx_type == SPGEMM_I32 && (M->nnz > 0x7fffffffLL || M->ncols >= 0x7fffffffLL)) {
         set_error(std::string(name) + ": nnz or ncols exceeds int32 index range"); return SPGEMM_ERR_INDEX_OVERFLOW;

@@ -336,8 +336,9 @@ template <class I, class V> struct Engine : EngineBase {
         int nheavy = 0;
         for (int t = kHeavyTier0; t < kTiers; ++t) nheavy += hist[t];
         if (nheavy && !allow_heavy) {
-            set_error("a column may hold more than " + std::to_string(cx.tun.hash_cap_max) +
-                      " distinct rows, above the shared-memory hash tables this call may use");
+            set_error("a column's entries summed over its sources (capped at the row count) exceed " +
+                      std::to_string(cx.tun.hash_cap_max) +
+                      ", the largest shared-memory hash table this call may use");
             return SPGEMM_ERR_INVALID;
         }
         TierCommon c = common_of(cx);

@@ -6,15 +6,17 @@
 // entry point serves them: every work buffer of the merge (per-column counts,
 // offsets, tier lists, scan partials, the part table) is carved from one
 // file-scope __device__ array of kNoAllocScratchBytes, and small device-to-host
-// reads land in a static host array. Each GPU that loads this library keeps
-// the array until the process exits.
+// reads land in a static host array, one per device. Each GPU that loads this
+// library keeps the array until the process exits.
 //
 // The array's address is looked up once per device (cudaGetSymbolAddress, with
 // that device current) on that device's first call, so that first call should
-// come before any stream capture. All calls share the array and it keeps the
-// last call's contents; the merge clears what it reads before writing. Calls
-// that overlap on the GPU (other streams, other host threads) race on the
-// array and must be serialised by the caller.
+// come before any stream capture. Every call synchronises its stream once, to
+// read the merged size. All calls on one device share that device's array and
+// host staging, and the array keeps the last call's contents; the merge clears
+// what it reads before writing. Calls on one device that overlap (other
+// streams, other host threads) race on both and must be serialised by the
+// caller; calls on different devices use different arrays.
 #include <mutex>
 #include <string>
 
@@ -32,7 +34,7 @@ constexpr int kMaxDevices = 64;
 void *g_scratch_addr[kMaxDevices] = {};
 int g_nsm[kMaxDevices] = {};
 std::mutex g_setup_mu;
-int32_t g_host_stage[1024];   // host staging of small device-to-host reads
+int32_t g_host_stage[kMaxDevices][1024];   // host staging of small device-to-host reads
 
 }  // namespace
 
@@ -62,5 +64,5 @@ extern "C" spgemm_status spgemm_merge_noalloc(const spgemm_csc *parts, int npart
     }
     return merge_noalloc_dispatch(parts, nparts, out, stream,
                                   static_cast<unsigned char *>(g_scratch_addr[dev]),
-                                  kNoAllocScratchBytes, g_host_stage, g_nsm[dev]);
+                                  kNoAllocScratchBytes, g_host_stage[dev], g_nsm[dev]);
 }

@@ -259,7 +259,81 @@ def test_absterm_bounds_value():
     np.testing.assert_allclose(ab, Sd[C.rowidx, cols], rtol=1e-13)
 
 
+def test_nterm_is_structure_product():
+    # n_ij = |{k : A(i,k) != 0 and B(k,j) != 0}| = (S_A S_B)(i, j), the dense
+    # integer product of the 0/1 structure matrices; over a k-stage the
+    # product of the stage's slices. Values are chosen so that some sums
+    # cancel to zero (the count still holds: structure, not value).
+    for seed, (m, k, n, d) in enumerate([(20, 20, 20, 0.3), (37, 11, 23, 0.5), (9, 40, 5, 0.2)]):
+        A = rand_csc(m, k, d, 300 + seed)
+        B = rand_csc(k, n, d, 400 + seed)
+        A.vals[::3] *= -1.0
+        SA = (A.to_dense() != 0).astype(np.int64)
+        SB = (B.to_dense() != 0).astype(np.int64)
+        for krange in (None, (k // 3, k - k // 4)):
+            C, nt = oracle.spgemm(A, B, krange=krange, with_nterm=True)
+            k0, k1 = (0, k) if krange is None else krange
+            N = SA[:, k0:k1] @ SB[k0:k1, :]
+            cols = np.repeat(np.arange(n), C.col_counts())
+            assert np.array_equal(nt, N[C.rowidx, cols])
+            assert np.all(nt >= 1)
+            # every reached entry is listed once: the structure is N > 0
+            assert int((N > 0).sum()) == C.nnz
+            # the counts of a column add up to its flops
+            f = oracle.flops_per_column(A, B, krange)
+            assert np.array_equal(np.bincount(cols, weights=nt, minlength=n).astype(np.int64), f)
+            # the three-tuple form returns the same C and scale
+            C2, ab, nt2 = oracle.spgemm(A, B, krange=krange, with_absterm=True, with_nterm=True)
+            assert np.array_equal(C2.rowidx, C.rowidx) and np.array_equal(nt2, nt)
+
+
 # ----------------------------------------------------------------------- c3 plan
+
+def test_plan_ranges_additive_equals_plan_batches():
+    rng = np.random.default_rng(93)
+    for trial in range(300):
+        n = int(rng.integers(0, 12))
+        w = rng.integers(0, 10, n)
+        cap = int(rng.integers(1, 25))
+        pre = np.concatenate([[0], np.cumsum(w)])
+        got = oracle.plan_ranges(lambda a, b: int(pre[b] - pre[a]), n, cap)
+        ref = oracle.plan_batches(w, cap)
+        if ref is None:
+            assert got is None
+        else:
+            assert np.array_equal(got, ref)
+
+
+def test_plan_ranges_minimal_for_max_costs():
+    # a cost with a maximum over "stages" (like a batch that keeps the largest
+    # of several partial products): monotone under range growth but not a sum;
+    # greedy extension still gives the fewest contiguous ranges (brute force)
+    import itertools
+    rng = np.random.default_rng(94)
+    for trial in range(200):
+        n = int(rng.integers(1, 8))
+        s = int(rng.integers(1, 4))
+        base = rng.integers(0, 6, n)
+        d = rng.integers(0, 6, (s, n))
+        cap = int(rng.integers(3, 30))
+
+        def cost(a, b):
+            return int(base[a:b].sum() + max(d[t, a:b].sum() for t in range(s)))
+
+        got = oracle.plan_ranges(cost, n, cap)
+        best = None
+        for cuts in itertools.product([0, 1], repeat=n - 1):
+            starts = [0] + [i + 1 for i in range(n - 1) if cuts[i]] + [n]
+            if all(cost(starts[i], starts[i + 1]) <= cap for i in range(len(starts) - 1)):
+                if best is None or len(starts) < best:
+                    best = len(starts)
+        if best is None:
+            assert got is None
+        else:
+            assert got is not None and len(got) == best
+            assert got[0] == 0 and got[-1] == n
+            assert all(cost(got[i], got[i + 1]) <= cap for i in range(len(got) - 1))
+
 
 def test_plan_batches_greedy_is_minimal_and_valid():
     rng = np.random.default_rng(91)

@@ -85,9 +85,66 @@ def test_noalloc_merge_rejects_inputs_beyond_its_scratch():
     rng = np.random.default_rng(3)
     rows = rng.choice(50_000, 9000, replace=False)
     dense_col = from_coo(50_000, 2, rows, np.zeros(rows.size, np.int64), np.ones(rows.size))
-    with pytest.raises(spg.SpgemmError, match="distinct rows"):
+    with pytest.raises(spg.SpgemmError, match="8192"):
         spg.merge_noalloc([to_dev(dense_col)])
     # and the entry point still works afterwards
     parts = parts_of(500, 400, 2, 0.01, 7)
     dev = [to_dev(p) for p in parts]
     same_result(host_csc(spg.merge_noalloc(dev)), host_csc(spg.merge(dev)), exact=False)
+
+
+def _same_rows_parts(nrows, rows_per_part, nparts, seed):
+    """nparts parts of one column, each holding the same rows_per_part rows
+    (different values): they merge to rows_per_part rows, while the entries
+    summed over the parts are nparts * rows_per_part."""
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(nrows, rows_per_part, replace=False)
+    out = []
+    for t in range(nparts):
+        v = rng.standard_normal(rows.size)
+        p = from_coo(nrows, 3, rows, np.ones(rows.size, np.int64), v)
+        out.append(shuffle_within_columns(p, seed + t))
+    return out
+
+
+def test_noalloc_limit_is_entries_over_parts_not_distinct_rows():
+    """The documented limit: per column, entries summed over the parts (capped
+    at nrows) at most 8192. 4 parts of the same 2,000 rows (8,000 entries) are
+    merged; 4 parts of the same 3,000 rows (12,000 entries, still 3,000
+    distinct rows) are refused."""
+    ok = _same_rows_parts(50_000, 2000, 4, 11)
+    dev = [to_dev(p) for p in ok]
+    got = spg.merge_noalloc(dev)
+    torch.cuda.synchronize()
+    same_result(host_csc(got), oracle.merge(ok), exact=False)
+    assert int(got.nnz) == 2000
+    over = _same_rows_parts(50_000, 3000, 4, 12)
+    with pytest.raises(spg.SpgemmError, match="8192"):
+        spg.merge_noalloc([to_dev(p) for p in over])
+    # the row-count cap: with nrows <= 8192 every column is accepted
+    small = _same_rows_parts(6000, 3000, 4, 13)
+    got = spg.merge_noalloc([to_dev(p) for p in small])
+    torch.cuda.synchronize()
+    same_result(host_csc(got), oracle.merge(small), exact=False)
+
+
+def test_noalloc_merge_of_k_stage_partials():
+    """The k-split use: the parts are the 4 stage products D_t = A(:, K_t)
+    A(K_t, :) of a small R-MAT A*A (Algorithm 1's stages), which share most
+    of their rows column by column; the merge must equal A*A (oracle) and
+    spgemm_merge, on two calls in a row."""
+    import workloads as W
+    A = W.rmat(11, 8, 20108599, index_dtype=np.int32, value_dtype=np.float64)
+    stages = [oracle.spgemm(A, A, krange=kr) for kr in oracle.stage_ranges(A.ncols, 4)]
+    parts = [CSC(p.nrows, p.ncols, p.colptr.astype(np.int32), p.rowidx.astype(np.int32), p.vals)
+             for p in stages]
+    ref, ab = oracle.spgemm(A, A, with_absterm=True)
+    dev = [to_dev(p) for p in parts]
+    for _ in range(2):
+        got = spg.merge_noalloc(dev)
+        alloc = spg.merge(dev)
+        torch.cuda.synchronize()
+        same_result(host_csc(got), host_csc(alloc), exact=False)
+        g = oracle.canonical(host_csc(got))
+        assert np.array_equal(g.colptr, ref.colptr) and np.array_equal(g.rowidx, ref.rowidx)
+        assert np.all(np.abs(g.vals - ref.vals) <= 1e-12 * ab + 1e-300)
