@@ -175,9 +175,9 @@ typedef struct {
  * Per-phase statistics of a plan (kernel launches always; device time only
  * while timing is enabled). Phases: 0 flop count + binning, 1 symbolic hash
  * tiers, 2 symbolic bitmap (heavy columns), 3 scans, 4 row-panel copy of A,
- * 5 numeric hash tiers, 6 numeric dense row panels, 7 stage merge,
- * 8 backward. Times come from CUDA events recorded on the stream each phase
- * was launched on.
+ * 5 numeric hash tiers, 6 numeric heavy columns (dense row panels and hash
+ * row ranges), 7 stage merge, 8 backward. Times come from CUDA events
+ * recorded on the stream each phase was launched on.
  */
 #define SPGEMM_NUM_PHASES 9
 typedef struct {

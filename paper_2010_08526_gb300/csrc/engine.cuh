@@ -157,6 +157,8 @@ template <class I, class V> struct Engine : EngineBase {
         set_smem(k_num_heavy<SrcPartsRange<I, V>, SrcPartsRange<I, V>, 2>, mx);
         set_smem(k_num_heavy<SrcPanelRange<I, V>, SrcColRange<I, V>, 3>, mx);
         set_smem(k_num_heavy<SrcPartsRange<I, V>, SrcPartsRange<I, V>, 3>, mx);
+        set_smem(k_num_heavy32<I, V, 1>, mx);
+        set_smem(k_num_heavy32<I, V, 2>, mx);
         set_smem(k_sort_block<I, V, 1024>, mx);
         set_smem(k_sort_block<I, V, 8192>, mx);
         set_smem(k_sort_items<I, V, 8192>, mx);
@@ -420,6 +422,27 @@ template <class I, class V> struct Engine : EngineBase {
                 const int stat = (int)sizeof(BlockShared<V, 512>) + 256;
                 const int per_sm = (3 * (smem + stat) <= 227 * 1024) ? 3 : 2;
                 const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * per_sm));
+                if constexpr (std::is_same<RSrc, SrcPanelRange<I, V>>::value) {
+                    // products: all heavy items in the kernel with 32-bit
+                    // offsets (every entry index < nnz(A) < 2^31)
+                    if (da.lean_dense) {
+                        const int dsm = dense_smem(cx);
+                        const int dstat = (int)sizeof(DenseShared<V>) + 256;
+                        const int dper = std::max(1, std::min(2, (227 * 1024) / (dsm + dstat)));
+                        const int dblocks = (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * dper));
+                        const int tdd = cx.tbegin(cx.ph_dense, st);
+                        if (dper >= 2)
+                            k_num_heavy32<I, V, 2><<<dblocks, kDenseChunk, dsm, st>>>(da, c, items, item_order,
+                                                                                     n_items_dev, o.rows, o.vals);
+                        else
+                            k_num_heavy32<I, V, 1><<<dblocks, kDenseChunk, dsm, st>>>(da, c, items, item_order,
+                                                                                     n_items_dev, o.rows, o.vals);
+                        cx.tend(tdd, st);
+                        cx.launched();
+                        SPG_CK(cudaGetLastError());
+                        return SPGEMM_OK;
+                    }
+                }
                 const int td = cx.tbegin(cx.ph_dense, st);
                 if (per_sm == 3)
                     k_num_heavy<RSrc, HS, 3><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items_dev,
@@ -458,6 +481,7 @@ template <class I, class V> struct Engine : EngineBase {
         a.apc_off = ps.apc_off.as<int32_t>();
         a.apc_row = ps.apc_row.as<uint32_t>();
         a.apc_val = ps.apc_val.as<V>();
+        a.lean_dense = ps.A.nnz < (int64_t(1) << 31) ? 1 : 0;
         return a;
     }
 

@@ -100,6 +100,7 @@ template <class I, class V> struct GemmArgs {
     const int32_t *apc_off;
     const uint32_t *apc_row;  // global rows
     const V *apc_val;
+    int lean_dense;           // heavy items may use 32-bit entry offsets (nnz(A) < 2^31)
 };
 
 template <class I, class V> struct PartsArgs {
@@ -1733,3 +1734,5 @@ template <class V> __global__ void k_fill_zero(V *p, int64_t n) {
 }
 
 }  // namespace spg
+
+#include "dense_items.cuh"

@@ -130,6 +130,30 @@ def test_heavy_types(vt):
     check_product(A, A, f"heavy {vt.__name__}", tuning=tun)
 
 
+@pytest.mark.parametrize("vt", [np.float32, np.float64, np.int64])
+def test_heavy_dense_items_with_cancelling_sums(vt):
+    """Dense row-panel items whose sums cancel to exactly zero, and explicit
+    zero entries: the structural nonzeros of C include entries whose value is
+    0 (every (i, j) reached by a product is kept), so these items cannot be
+    compacted by value; the exact per-panel counts decide. Values in
+    {-1, 0, 1}: every sum is an exact integer in any order."""
+    rng = np.random.default_rng(61)
+    A = skewed(4000, 4000, 62, hubs=4, hub_deg=3000, base=6, index_dtype=np.int32)
+    vals = rng.choice(np.array([-1.0, 1.0, 1.0, -1.0, 0.0]), A.nnz)
+    A = CSC(A.nrows, A.ncols, A.colptr, A.rowidx, vals.astype(vt))
+    tun = spg.Tuning(hash_max_cap=256, panel_rows=1024)
+    got, info = run(A, A, tuning=tun)
+    assert info["heavy_columns"] > 0
+    ref = oracle.spgemm(A, A)
+    assert int((np.asarray(ref.vals) == 0).sum()) > 1000   # many exact zeros are structural
+    assert_matches(got, ref, exact=True, label=f"cancelling heavy {np.dtype(vt).name}")
+    # all-zero values: every entry of C is structural and zero
+    Z = CSC(A.nrows, A.ncols, A.colptr, A.rowidx, np.zeros(A.nnz, vt))
+    gz, _ = run(Z, Z, tuning=tun)
+    rz = oracle.spgemm(Z, Z)
+    assert_matches(gz, rz, exact=True, label="all-zero heavy")
+
+
 def test_tuning_variants():
     A = skewed(4000, 3000, 31, hubs=2, hub_deg=1500)
     B = skewed(3000, 3500, 32, hubs=2, hub_deg=1200)
