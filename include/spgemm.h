@@ -131,6 +131,33 @@ typedef struct {
     int reserved[2];
 } spgemm_tuning;
 
+/*
+ * Caller-supplied memory for a plan's workspace. The paper's processes hold
+ * the batch buffers of Algorithm 4 inside a fixed memory budget (Sec. IV-A);
+ * here the application that owns the device memory (for example PyTorch's
+ * caching allocator) hands it to the library through these callbacks.
+ *   alloc(ctx, bytes, kind) returns `bytes` of memory of `kind`, aligned to
+ *     256 bytes, or NULL when it cannot (the call then fails with
+ *     SPGEMM_ERR_OOM and frees what it had allocated for the failed step);
+ *   free(ctx, p, bytes, kind) returns a block that alloc gave. The library
+ *     calls it only after the device has finished every use of the block
+ *     (it synchronises the device first), when a buffer grows or when the
+ *     plan is destroyed.
+ * Both run on the calling host thread with the plan's device current, from
+ * inside the library call that needs the memory; they must not call back
+ * into the library. kind: SPGEMM_MEM_DEVICE for device memory,
+ * SPGEMM_MEM_PINNED_HOST for page-locked host memory (the host ring of
+ * spgemm_run_batched and small staging reads).
+ */
+typedef enum { SPGEMM_MEM_DEVICE = 0, SPGEMM_MEM_PINNED_HOST = 1 } spgemm_mem_kind;
+typedef void *(*spgemm_alloc_fn)(void *ctx, size_t bytes, int kind);
+typedef void (*spgemm_free_fn)(void *ctx, void *p, size_t bytes, int kind);
+typedef struct {
+    spgemm_alloc_fn alloc;   /* both non-NULL */
+    spgemm_free_fn free;
+    void *ctx;               /* passed back unchanged */
+} spgemm_allocator;
+
 typedef struct {
     size_t budget_bytes;     /* device memory for A, B, workspace and batch outputs;
                                 0 = 80% of the free device memory at plan time */
@@ -151,6 +178,8 @@ typedef struct {
                                 to the product, the k-stage merge and spgemm_run_batched,
                                 and spgemm_backward refuses them */
     int merge_mode;          /* spgemm_merge_t (0 = merge at the end); used when kstages > 1 */
+    const spgemm_allocator *allocator; /* workspace memory of the plan (copied at plan
+                                creation); NULL: cudaMalloc and cudaHostAlloc */
 } spgemm_opts;
 
 typedef struct spgemm_plan_s spgemm_plan;
@@ -196,9 +225,15 @@ const char *spgemm_version(void);
  * spgemm_plan_create -- validate A and B and set up a plan for C = A * B.
  * Checks A.ncols == B.nrows, equal index and value types, nnz == colptr[ncols]
  * (one device read) and, when validate != 0, monotone colptr and rows in range
- * (a device check, one synchronisation). Allocates plan workspace with
- * cudaMalloc. A and B must stay valid and unchanged for the plan's lifetime.
- * Errors: SPGEMM_ERR_INVALID, SPGEMM_ERR_OOM, SPGEMM_ERR_CUDA.
+ * (a device check, one synchronisation). The plan is the state of one product
+ * C = A * B (the problem of Sec. II-B) through Algorithm 3's symbolic step and
+ * Algorithm 4's batches. Plan workspace, and the pinned host ring of
+ * spgemm_run_batched, come from opts->allocator when it is set, else from
+ * cudaMalloc / cudaHostAlloc; every later call on the plan uses the same
+ * allocator. A and B must stay valid and unchanged for the plan's lifetime.
+ * Errors: SPGEMM_ERR_INVALID (also an allocator with a NULL callback),
+ * SPGEMM_ERR_OOM (an allocation failed; nothing the failed call allocated is
+ * kept), SPGEMM_ERR_CUDA.
  */
 spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B,
                                  const spgemm_opts *opts, int validate,

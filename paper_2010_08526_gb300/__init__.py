@@ -37,10 +37,11 @@ from .core import (
     backward,
     SpGEMMFn,
     Multi,
+    TorchAllocator,
 )
 
 __all__ = [
     "SpgemmError", "load", "Csc", "Plan", "Tuning", "spgemm", "merge", "merge_noalloc", "prune", "run_batched", "transpose",
     "spgemm_aat", "run_row_batched",
-    "backward", "SpGEMMFn", "Multi",
+    "backward", "SpGEMMFn", "Multi", "TorchAllocator",
 ]

@@ -33,6 +33,15 @@ class SpgemmTuning(ctypes.Structure):
     ]
 
 
+MEM_DEVICE, MEM_PINNED_HOST = 0, 1
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int)
+
+
+class SpgemmAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
 class SpgemmOpts(ctypes.Structure):
     _fields_ = [
         ("budget_bytes", ctypes.c_size_t), ("kstages", ctypes.c_int), ("ring_depth", ctypes.c_int),
@@ -40,6 +49,7 @@ class SpgemmOpts(ctypes.Structure):
         ("sort_output", ctypes.c_int), ("tuning", ctypes.POINTER(SpgemmTuning)),
         ("prune", ctypes.c_int), ("prune_threshold", ctypes.c_double), ("prune_topk", ctypes.c_int64),
         ("semiring", ctypes.c_int), ("merge_mode", ctypes.c_int),
+        ("allocator", ctypes.POINTER(SpgemmAllocator)),
     ]
 
 

@@ -107,10 +107,75 @@ _SEMIRINGS = {"plus_times": 0, "min_plus": 1, "or_and": 2}
 _MERGES = {"end": 0, "incremental": 1}
 
 
+class TorchAllocator:
+    """Plan workspace from PyTorch (the spgemm_allocator callbacks): device
+    blocks from torch's caching allocator, pinned host blocks from its pinned
+    memory allocator. Each block is a uint8 tensor kept alive here until the
+    library frees it, so the memory shows up in torch's accounting
+    (torch.cuda.memory_allocated) and returns to torch's pool afterwards.
+    Counters: n_alloc, n_free, live (blocks held), bytes_live."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.blocks = {}
+        self.n_alloc = 0
+        self.n_free = 0
+        self.bytes_live = 0
+        self._alloc_cb = C.ALLOC_FN(self._alloc)
+        self._free_cb = C.FREE_FN(self._free)
+        self.struct = C.SpgemmAllocator(self._alloc_cb, self._free_cb, None)
+
+    def allocate(self, nbytes: int, kind: int):
+        """A tensor of nbytes bytes of the kind asked for, or None when it
+        cannot be had (subclasses may refuse on purpose)."""
+        if kind == C.MEM_DEVICE:
+            return torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        return torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+
+    def _alloc(self, ctx, nbytes, kind):
+        try:
+            t = self.allocate(int(nbytes), int(kind))
+        except Exception:   # out of memory: the library reports SPGEMM_ERR_OOM
+            t = None
+        if t is None:
+            return None
+        p = int(t.data_ptr())
+        self.blocks[p] = t
+        self.n_alloc += 1
+        self.bytes_live += int(nbytes)
+        return p
+
+    def _free(self, ctx, p, nbytes, kind):
+        t = self.blocks.pop(int(p or 0), None)
+        if t is not None:
+            self.n_free += 1
+            self.bytes_live -= int(nbytes)
+
+    @property
+    def live(self) -> int:
+        return len(self.blocks)
+
+
+def _allocator_of(allocator, device):
+    """allocator: "torch" (default) for a TorchAllocator on the plan's
+    device, None for the library's own cudaMalloc / cudaHostAlloc, or an
+    object with a .struct (a TorchAllocator or one built the same way)."""
+    if allocator is None:
+        return None
+    if isinstance(allocator, str):
+        if allocator != "torch":
+            raise ValueError(f"unknown allocator {allocator!r}")
+        return TorchAllocator(device)
+    return allocator
+
+
 def _opts(budget=None, kstages=1, tuning: Optional[Tuning] = None, ring_depth=0,
           host_slot_bytes=0, host_slots=0, sort_output=False, prune=None, semiring="plus_times",
-          merge="end"):
+          merge="end", allocator=None):
     o = C.SpgemmOpts()
+    if allocator is not None:
+        o.allocator = ctypes.pointer(allocator.struct)
     o.budget_bytes = int(budget or 0)
     o.kstages = int(kstages)
     o.ring_depth = int(ring_depth)
@@ -149,7 +214,7 @@ class Plan:
                  tuning: Optional[Tuning] = None, validate: bool = False, ring_depth: int = 0,
                  host_slot_bytes: int = 0, host_slots: int = 0, sort_output: bool = False,
                  prune: Optional[tuple] = None, semiring: str = "plus_times", merge: str = "end",
-                 stream: Optional[torch.cuda.Stream] = None):
+                 stream: Optional[torch.cuda.Stream] = None, allocator="torch"):
         """sort_output: rows sorted inside every column of C. prune = (threshold,
         topk): run_batched prunes each batch on the device before the copy
         (see prune()). semiring: "plus_times", "min_plus" (C(i,j) = min_k
@@ -157,13 +222,16 @@ class Plan:
         has A(i,k) != 0 and B(k,j) != 0, else 0, any value type). merge (kstages > 1): "end" keeps the
         s stage partials of a batch and merges them once; "incremental"
         merges each stage into the running sum as it is produced (less memory
-        when the stages overlap, more merge work)."""
+        when the stages overlap, more merge work). allocator: where the plan's
+        workspace comes from: "torch" (PyTorch's allocators, the default),
+        None (the library's cudaMalloc / cudaHostAlloc) or a TorchAllocator."""
         lib = load()
         self._lib = lib
         self.A, self.B = A, B
         self._sa, self._sb = A.struct(), B.struct()
+        self.allocator = _allocator_of(allocator, A.device)
         self._opts, self._tun = _opts(budget, kstages, tuning, ring_depth, host_slot_bytes,
-                                      host_slots, sort_output, prune, semiring, merge)
+                                      host_slots, sort_output, prune, semiring, merge, self.allocator)
         h = ctypes.c_void_p()
         check(lib.spgemm_plan_create(ctypes.byref(self._sa), ctypes.byref(self._sb),
                                      ctypes.byref(self._opts), int(validate),
@@ -496,14 +564,15 @@ class Multi:
     """
 
     def __init__(self, As: List[Csc], Bs: List[Csc], *, tuning: Optional[Tuning] = None,
-                 stream=None):
+                 stream=None, allocator="torch"):
         lib = load()
         self._lib = lib
         self.As, self.Bs = As, Bs
         n = len(As)
         self._sa = (C.SpgemmCsc * n)(*[a.struct() for a in As])
         self._sb = (C.SpgemmCsc * n)(*[b.struct() for b in Bs])
-        self._opts, self._tun = _opts(tuning=tuning)
+        self.allocator = _allocator_of(allocator, As[0].device)
+        self._opts, self._tun = _opts(tuning=tuning, allocator=self.allocator)
         h = ctypes.c_void_p()
         check(lib.spgemm_multi_create(n, self._sa, self._sb, ctypes.byref(self._opts),
                                       _stream_handle(stream), ctypes.byref(h)))

@@ -16,8 +16,46 @@ static thread_local std::string g_err = "no error";
 void set_error(const std::string &msg) { g_err = msg; }
 
 spgemm_status cuda_fail(cudaError_t e, const char *where) {
+    if (e == cudaErrorMemoryAllocation) {
+        g_err = std::string("allocation failed in ") + where;
+        return SPGEMM_ERR_OOM;
+    }
     g_err = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
     return SPGEMM_ERR_CUDA;
+}
+
+thread_local AllocFns tl_alloc;
+
+void *alloc_mem(const AllocFns &a, size_t bytes, int kind, cudaError_t &e) {
+    void *p = nullptr;
+    if (a.alloc) {
+        p = a.alloc(a.ctx, bytes, kind);
+        if (!p) { e = cudaErrorMemoryAllocation; return nullptr; }
+        if (reinterpret_cast<uintptr_t>(p) % 256) {   // the callbacks promise 256-byte alignment
+            a.free(a.ctx, p, bytes, kind);
+            e = cudaErrorInvalidValue;
+            return nullptr;
+        }
+        e = cudaSuccess;
+        return p;
+    }
+    e = kind == SPGEMM_MEM_DEVICE ? cudaMalloc(&p, bytes) : cudaHostAlloc(&p, bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // a failed allocation must not look like a failed launch later
+        p = nullptr;
+    }
+    return p;
+}
+
+void free_mem(const AllocFns &a, void *p, size_t bytes, int kind) {
+    if (a.alloc) {
+        // the caller's allocator may hand the block out again at once: every
+        // use of it on the device must have finished (as cudaFree ensures)
+        cudaDeviceSynchronize();
+        a.free(a.ctx, p, bytes, kind);
+        return;
+    }
+    if (kind == SPGEMM_MEM_DEVICE) cudaFree(p); else cudaFreeHost(p);
 }
 
 size_t PlanState::workspace_bytes() const {
@@ -125,6 +163,9 @@ spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B, const
             set_error("the min-plus semiring needs floating-point values"); return SPGEMM_ERR_INVALID;
         }
     }
+    if (opts && opts->allocator && (!opts->allocator->alloc || !opts->allocator->free)) {
+        set_error("an allocator needs both its alloc and free callbacks"); return SPGEMM_ERR_INVALID;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -140,6 +181,13 @@ spgemm_status spgemm_plan_create(const spgemm_csc *A, const spgemm_csc *B, const
     PlanState &ps = plan->ps;
     ps.A = *A; ps.B = *B;
     if (opts) ps.opts = *opts;
+    ps.opts.allocator = nullptr;   // copied below; the caller's struct need not outlive the call
+    if (opts && opts->allocator) {
+        ps.alloc.alloc = opts->allocator->alloc;
+        ps.alloc.free = opts->allocator->free;
+        ps.alloc.ctx = opts->allocator->ctx;
+    }
+    AllocScope scope(ps.alloc);
     ps.s = kst;
     ps.idx64 = A->idx_type == SPGEMM_I64;
     ps.vtype = A->val_type;
@@ -245,6 +293,7 @@ spgemm_status spgemm_plan_destroy(spgemm_plan *plan) {
 
 spgemm_status spgemm_symbolic(spgemm_plan *plan, cudaStream_t stream) {
     if (!plan) { set_error("plan is NULL"); return SPGEMM_ERR_INVALID; }
+    AllocScope scope(plan->ps.alloc);
     return plan->ps.eng->symbolic(plan->ps, stream);
 }
 
@@ -297,6 +346,7 @@ spgemm_status spgemm_plan_column_counts(const spgemm_plan *plan, int64_t *counts
 spgemm_status spgemm_numeric(spgemm_plan *plan, int64_t t, spgemm_csc *C, cudaStream_t stream) {
     if (!plan || !C) { set_error("NULL argument"); return SPGEMM_ERR_INVALID; }
     PlanState &ps = plan->ps;
+    AllocScope scope(ps.alloc);
     if (!ps.have_symbolic) { set_error("call spgemm_symbolic first"); return SPGEMM_ERR_STATE; }
     if (t < 0 || t >= (int64_t)ps.batches.size()) { set_error("batch out of range"); return SPGEMM_ERR_INVALID; }
     const Batch &b = ps.batches[(size_t)t];
@@ -320,6 +370,7 @@ spgemm_status spgemm_backward(spgemm_plan *plan, const spgemm_csc *G, void *dA_v
                               cudaStream_t stream) {
     if (!plan || !G) { set_error("NULL argument"); return SPGEMM_ERR_INVALID; }
     const PlanState &ps = plan->ps;
+    AllocScope scope(ps.alloc);
     spgemm_status s = check_csc(G, "G", false);
     if (s != SPGEMM_OK) return s;
     if (G->nrows != ps.m || G->ncols != ps.n) { set_error("G must have C's shape"); return SPGEMM_ERR_INVALID; }
@@ -461,6 +512,9 @@ spgemm_status spgemm_multi_create(int nprob, const spgemm_csc *As, const spgemm_
                   "(semiring, sort_output and prune are plan options)");
         return SPGEMM_ERR_INVALID;
     }
+    if (opts && opts->allocator && (!opts->allocator->alloc || !opts->allocator->free)) {
+        set_error("an allocator needs both its alloc and free callbacks"); return SPGEMM_ERR_INVALID;
+    }
     int dev = 0;
     cudaDeviceProp prop;
     cudaError_t e = cudaGetDevice(&dev);
@@ -469,6 +523,12 @@ spgemm_status spgemm_multi_create(int nprob, const spgemm_csc *As, const spgemm_
     auto *mh = new (std::nothrow) spgemm_multi_s();
     if (!mh) { set_error("host allocation failed"); return SPGEMM_ERR_OOM; }
     MultiState &ms = mh->ms;
+    if (opts && opts->allocator) {
+        ms.alloc.alloc = opts->allocator->alloc;
+        ms.alloc.free = opts->allocator->free;
+        ms.alloc.ctx = opts->allocator->ctx;
+    }
+    AllocScope scope(ms.alloc);
     ms.nprob = nprob;
     ms.idx64 = As[0].idx_type == SPGEMM_I64;
     ms.vtype = As[0].val_type;
@@ -496,6 +556,7 @@ spgemm_status spgemm_multi_destroy(spgemm_multi *m) {
 spgemm_status spgemm_multi_run(spgemm_multi *m, int use_graph, cudaStream_t stream) {
     if (!m) { set_error("NULL argument"); return SPGEMM_ERR_INVALID; }
     MultiState &ms = m->ms;
+    AllocScope scope(ms.alloc);
     cudaError_t e;
     if (!use_graph) return ms.enqueue(ms, stream);
     // graphs are captured on a private stream (the legacy default stream cannot

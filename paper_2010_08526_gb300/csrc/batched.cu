@@ -27,6 +27,7 @@ extern "C" spgemm_status spgemm_run_batched(spgemm_plan *plan, spgemm_sink_fn si
                                             cudaStream_t compute, cudaStream_t copy) {
     if (!plan || !sink) { set_error("NULL argument"); return SPGEMM_ERR_INVALID; }
     PlanState &ps = plan->ps;
+    AllocScope scope(ps.alloc);
     if (!ps.have_symbolic) { set_error("call spgemm_symbolic first"); return SPGEMM_ERR_STATE; }
     const int R = ps.opts.ring_depth > 0 ? ps.opts.ring_depth : 2;
     const int H = ps.opts.host_slots >= 2 ? ps.opts.host_slots : 3;

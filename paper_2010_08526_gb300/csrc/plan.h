@@ -11,37 +11,68 @@
 
 namespace spg {
 
-// A grow-only device buffer.
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-    cudaError_t ensure(size_t want) {
-        if (want <= bytes && p) return cudaSuccess;
-        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
-        if (want == 0) want = 16;
-        cudaError_t e = cudaMalloc(&p, want);
-        if (e == cudaSuccess) bytes = want; else p = nullptr;
-        return e;
-    }
-    void release() { if (p) cudaFree(p); p = nullptr; bytes = 0; }
-    template <class T> T *as() const { return static_cast<T *>(p); }
+// The allocator a buffer takes its memory from: the callbacks of
+// spgemm_allocator, or (alloc == nullptr) cudaMalloc / cudaHostAlloc.
+struct AllocFns {
+    spgemm_alloc_fn alloc = nullptr;
+    spgemm_free_fn free = nullptr;
+    void *ctx = nullptr;
 };
 
-// A grow-only pinned host buffer.
-struct HostBuf {
+// The allocator of the plan whose call is running on this thread (a plan is
+// used by one host thread at a time); set for the length of a call by
+// AllocScope. Buffers remember the allocator that produced them and give
+// their memory back to it.
+extern thread_local AllocFns tl_alloc;
+struct AllocScope {
+    AllocFns saved;
+    explicit AllocScope(const AllocFns &a) : saved(tl_alloc) { tl_alloc = a; }
+    ~AllocScope() { tl_alloc = saved; }
+};
+
+// Memory of `kind` from the current allocator; cudaErrorMemoryAllocation when
+// it fails (no CUDA error state is left behind).
+void *alloc_mem(const AllocFns &a, size_t bytes, int kind, cudaError_t &e);
+void free_mem(const AllocFns &a, void *p, size_t bytes, int kind);
+
+// A grow-only buffer of device (KIND = SPGEMM_MEM_DEVICE) or pinned host
+// memory; it owns its block (moved, never copied) and frees it when destroyed.
+template <int KIND> struct Buf {
     void *p = nullptr;
     size_t bytes = 0;
+    AllocFns how;
+    Buf() = default;
+    Buf(const Buf &) = delete;
+    Buf &operator=(const Buf &) = delete;
+    Buf(Buf &&o) noexcept : p(o.p), bytes(o.bytes), how(o.how) { o.p = nullptr; o.bytes = 0; }
+    Buf &operator=(Buf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; bytes = o.bytes; how = o.how;
+            o.p = nullptr; o.bytes = 0;
+        }
+        return *this;
+    }
+    ~Buf() { release(); }
     cudaError_t ensure(size_t want) {
         if (want <= bytes && p) return cudaSuccess;
-        if (p) { cudaFreeHost(p); p = nullptr; bytes = 0; }
+        release();
         if (want == 0) want = 16;
-        cudaError_t e = cudaHostAlloc(&p, want, cudaHostAllocDefault);
+        cudaError_t e = cudaSuccess;
+        how = tl_alloc;
+        p = alloc_mem(how, want, KIND, e);
         if (e == cudaSuccess) bytes = want; else p = nullptr;
         return e;
     }
-    void release() { if (p) cudaFreeHost(p); p = nullptr; bytes = 0; }
+    void release() {
+        if (p) free_mem(how, p, bytes, KIND);
+        p = nullptr;
+        bytes = 0;
+    }
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
+using DevBuf = Buf<SPGEMM_MEM_DEVICE>;
+using HostBuf = Buf<SPGEMM_MEM_PINNED_HOST>;
 
 int64_t scan_partials_len(int64_t n);
 
@@ -155,6 +186,7 @@ struct EngineBase;
 struct PlanState {
     spgemm_csc A{}, B{};
     spgemm_opts opts{};
+    AllocFns alloc;          // workspace allocator (opts->allocator, copied)
     Tuning tun;
     int idx64 = 0, vtype = 0;
     int64_t m = 0, k = 0, n = 0;
@@ -249,6 +281,7 @@ namespace spg {
 // State of a multi-problem run (spgemm_multi).
 struct MultiState {
     int nprob = 0, idx64 = 0, vtype = 0, nsm = 148;
+    AllocFns alloc;          // workspace allocator (opts->allocator, copied)
     Tuning tun;
     DevBuf probs, f, cnt, colptr, tier, list, off, list2, off2, hist, cursor, err, scan_part;
     DevBuf rows, vals;

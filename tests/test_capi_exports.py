@@ -67,7 +67,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if not gcc or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime_api.h")):
         pytest.skip("needs gcc and the CUDA headers")
     structs = {"spgemm_csc": C.SpgemmCsc, "spgemm_tuning": C.SpgemmTuning, "spgemm_opts": C.SpgemmOpts,
-               "spgemm_plan_info": C.SpgemmPlanInfo, "spgemm_stats": C.SpgemmStats}
+               "spgemm_plan_info": C.SpgemmPlanInfo, "spgemm_stats": C.SpgemmStats,
+               "spgemm_allocator": C.SpgemmAllocator}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "spgemm.h"', "int main(void) {"]
     for cname, py in structs.items():
         src.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
@@ -138,3 +139,21 @@ def test_python_option_names():
         core._opts(semiring="max_times")
     assert core.Tuning(hybrid_sort=True).struct().hybrid_sort == 1
     assert core.Tuning().struct().hybrid_sort == 0
+
+
+def test_allocator_needs_both_callbacks_without_gpu():
+    """An allocator whose free callback is NULL is refused before any device
+    call (the library must be able to give back every block it takes)."""
+    from paper_2010_08526_gb300 import _capi as C
+    lib = C.load()
+    dummy = ctypes.c_void_p(64)      # never dereferenced: the checks come first
+    M = C.SpgemmCsc(4, 4, 0, dummy, None, None, 0, 0, 1)
+    al = C.SpgemmAllocator(C.ALLOC_FN(lambda ctx, n, k: None), C.FREE_FN(), None)
+    o = C.SpgemmOpts()
+    o.allocator = ctypes.pointer(al)
+    h = ctypes.c_void_p()
+    st = lib.spgemm_plan_create(ctypes.byref(M), ctypes.byref(M), ctypes.byref(o), 0, None, ctypes.byref(h))
+    assert st == 1 and not h.value
+    assert b"allocator" in lib.spgemm_last_error()
+    st = lib.spgemm_multi_create(1, ctypes.byref(M), ctypes.byref(M), ctypes.byref(o), None, ctypes.byref(h))
+    assert st == 1 and not h.value
