@@ -116,6 +116,14 @@ def algorithmic_bytes_dense(A, f, cnt, cap, si=4, sv=4):
     return b_bytes + a_bytes + c_bytes, int(dense.sum())
 
 
+def flops_host_ab(A, B):
+    """Multiplications per column of A*B."""
+    deg = np.diff(A.colptr.astype(np.int64))
+    cols = np.repeat(np.arange(B.ncols), np.diff(B.colptr.astype(np.int64)))
+    return np.bincount(cols, weights=deg[B.rowidx.astype(np.int64)].astype(np.float64),
+                       minlength=B.ncols).astype(np.int64)
+
+
 def flops_host(A):
     deg = np.diff(A.colptr.astype(np.int64))
     cols = np.repeat(np.arange(A.ncols), deg)
@@ -316,6 +324,7 @@ def run_gpu(args):
         del outs
         torch.cuda.empty_cache()
         kplan = spg.Plan(Ad, Ad, kstages=4)
+        kplan.set_timing(True)
         kinfo = kplan.symbolic()
         kouts = [kplan.alloc_batch(t) for t in range(kplan.nbatches)]
 
@@ -328,16 +337,28 @@ def run_gpu(args):
         ks_steps = max(1, args.steps // 2)
         k0 = torch.cuda.Event(enable_timing=True)
         k1 = torch.cuda.Event(enable_timing=True)
+        kplan.stats(reset=True)
         k0.record(st)
         for _ in range(ks_steps):
             kstep()
         k1.record(st)
         torch.cuda.synchronize()
         kms = k0.elapsed_time(k1) / ks_steps
+        kstats = kplan.stats(reset=True)
         kplan.check_errors()
+        # the sort-free hash merge (Sec. IV-D) on the HBM roofline: it reads
+        # every stage partial entry and writes every entry of C
+        mbytes = (int(kinfo["unmerged_nnz"]) + int(kinfo["nnz_c"])) * (4 + 4)
+        mms = kstats["ms"]["merge"] / ks_steps
         ks = {"value": 2 * F / (kms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": kms,
               "stages": 4, "nbatches": kinfo["nbatches"], "unmerged_nnz": kinfo["unmerged_nnz"],
-              "stage_buffer_nnz": kinfo["stage_buffer_nnz"], "merge": "end"}
+              "stage_buffer_nnz": kinfo["stage_buffer_nnz"], "merge": "end",
+              "phase_ms_per_step": {k: round(v / ks_steps, 3) for k, v in kstats["ms"].items() if v},
+              "merge_roofline": {"bound": "hbm", "algorithmic_bytes": mbytes, "merge_ms": mms,
+                                 "achieved": mbytes / (mms / 1e3) / 1e9 if mms else 0.0,
+                                 "peak": peaks()[0], "unit": "GB/s",
+                                 "frac": (mbytes / (mms / 1e3) / 1e9) / peaks()[0] if mms else 0.0,
+                                 "note": "sum_t nnz(D_t) + nnz(C) entries of (index + value)"}}
         del kouts
         kplan.close()
         torch.cuda.empty_cache()
@@ -410,6 +431,8 @@ def run_gpu(args):
         extras["or_and"].pop("_counts")
         extras["protein_2M"] = bench_protein(spg, torch, args, dev)
         extras["kmerge"] = bench_kmerge(spg, torch, args, A, dev)
+        extras["er4096"] = bench_config1(spg, torch, args, dev)
+        extras["aat_kmer"] = bench_aat(spg, torch, args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -443,7 +466,29 @@ def run_gpu(args):
             "cpu_baseline": cpu,
         }
         line.update(extras)
+        if extras:
+            line["configs"] = configs_summary(line)
         print(json.dumps(line))
+
+
+def configs_summary(line):
+    """One entry per benchmark configuration (the five workloads the
+    benchmark is specified on), with the GPU figure, its roofline where the
+    HBM bound applies, and the CPU oracle beside it."""
+    def pick(d, *keys):
+        return {k: d[k] for k in keys if d is not None and k in d}
+    p = line.get("protein_2M") or {}
+    return {
+        "1_er4096_fp64": pick(line.get("er4096"), "us_per_product", "value", "unit", "cpu_baseline", "note"),
+        "2_rmat20_fp32": {"value": line["value"], "unit": line["unit"], "ms_per_step": line["ms_per_step"],
+                          "roofline": line["roofline"], "e2e": line.get("e2e"),
+                          "ksplit4": line.get("ksplit4"), "cpu_baseline": line.get("cpu_baseline")},
+        "3_protein2M_24GB": pick(p, "value", "unit", "ms_per_step", "nbatches", "roofline_numeric", "e2e",
+                                 "cpu_baseline"),
+        "4_batched512_int64": pick(line.get("batched_vs_plain"), "multi_gflops", "multi_ms", "plain_ms",
+                                   "speedup", "cpu_baseline"),
+        "5_fwdbwd": pick(line.get("fwdbwd_vs_plain"), "fused_ms", "plain_ms", "speedup", "cpu_baseline"),
+    }
 
 
 def bench_multi(spg, torch, args):
@@ -481,9 +526,22 @@ def bench_multi(spg, torch, args):
     plain()
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
-    return {"problems": n, "flops": flops, "multi_ms": t_multi * 1e3, "plain_ms": t_plain * 1e3,
-            "speedup": t_plain / t_multi, "multi_gflops": 2 * flops / t_multi / 1e9,
-            "tuning": autotune.describe([(best, 0.0)])[0], "autotune_trials": autotune.describe(trials)}
+    r = {"problems": n, "flops": flops, "multi_ms": t_multi * 1e3, "plain_ms": t_plain * 1e3,
+         "speedup": t_plain / t_multi, "multi_gflops": 2 * flops / t_multi / 1e9,
+         "tuning": autotune.describe([(best, 0.0)])[0], "autotune_trials": autotune.describe(trials)}
+    if not args.no_cpu:
+        import oracle
+        sample = probs[:48]
+        sf = sum(int(flops_host(p).sum()) for p in sample)
+        t0 = time.perf_counter()
+        for p in sample:
+            oracle.spgemm(p, p)
+        dt = time.perf_counter() - t0
+        r["cpu_baseline"] = {"value": 2 * sf / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "seconds": dt,
+                             "sample": f"the first {len(sample)} of the {n} problems ({sf:.3e} multiplies), "
+                                       "int64 path counts"}
+    return r
 
 
 def bench_step(spg, torch, args, A, dev, note, B=None, **plan_kw):
@@ -550,13 +608,19 @@ def bench_kmerge(spg, torch, args, A, dev):
 
 
 def bench_protein(spg, torch, args, dev):
-    """The protein-similarity stand-in (2M x 2M, int64 indices, fp32, mean
-    degree 40, compression ~1): device step and the numeric phases' share of
-    the Gustavson-model bytes against the measured HBM copy peak."""
+    """Config 3, the protein-similarity stand-in (2M x 2M, int64 indices,
+    fp32, mean degree 40, compression ~1) at its 24 GB HBM output budget,
+    which forces b >= 4 column batches: the device step (symbolic + every
+    batch's numeric), the numeric phases against the HBM roofline, and the
+    batch loop end to end (A from pinned host memory, every batch streamed to
+    pinned host slots on a copy stream while the next one is computed)."""
     A = W.config3()
-    r = bench_step(spg, torch, args, A, dev, note="C = A*A, protein-similarity stand-in, 2,000,000^2, "
-                   "lognormal degrees (mean 40), int64 CSC, fp32")
+    budget = 24 << 30
+    r = bench_step(spg, torch, args, A, dev, budget=budget,
+                   note="C = A*A, protein-similarity stand-in, 2,000,000^2, lognormal degrees "
+                        "(mean 40), int64 CSC, fp32; 24 GB budget")
     cnt = r.pop("_counts")
+    r["budget_bytes"] = budget
     f = flops_host(A)
     nnzb = np.diff(A.colptr).astype(np.int64)
     si, sv = 8, 4
@@ -566,13 +630,142 @@ def bench_protein(spg, torch, args, dev):
     achieved = model / (num_ms / 1e3) / 1e9 if num_ms else 0.0
     r["roofline_numeric"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "algorithmic_bytes": model, "numeric_ms": num_ms}
+    # end to end through the batch loop, at the same budget
+    F = int(f.sum())
+    hostA = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (A.colptr, A.rowidx, A.vals)]
+    dA = spg.Csc(A.nrows, A.ncols, *[torch.empty_like(h, device=f"cuda:{dev}") for h in hostA])
+    eplan = spg.Plan(dA, dA, budget=budget, host_slot_bytes=1 << 30, host_slots=4)
+    cs = torch.cuda.Stream()
+    got = {"bytes": 0}
+
+    def sink(batch, c0, c1, arrs):
+        cp, ri, va = arrs
+        got["bytes"] += cp.nbytes + ri.nbytes + va.nbytes
+        return 0
+
+    def estep():
+        for h, d in zip(hostA, (dA.colptr, dA.rowidx, dA.vals)):
+            d.copy_(h, non_blocking=True)
+        eplan.symbolic()
+        got["bytes"] = 0
+        spg.run_batched(eplan, sink, copy=cs)
+        return got["bytes"]
+    estep()
+    torch.cuda.synchronize()
+    n = max(1, min(args.steps, 2))
+    t0 = time.perf_counter()
+    bo = 0
+    for _ in range(n):
+        bo = estep()
+    torch.cuda.synchronize()
+    edt = (time.perf_counter() - t0) / n
+    einfo = eplan.query()
+    eplan.close()
+    del dA
+    torch.cuda.empty_cache()
+    r["e2e"] = {"value": 2 * F / edt / 1e9, "unit": UNIT, "ms_per_step": edt * 1e3,
+                "nbatches": int(einfo["nbatches"]),
+                "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in hostA),
+                "d2h_bytes_per_step": bo, "d2h_gbs": bo / edt / 1e9,
+                "note": "A copied from pinned host memory, symbolic, then every batch streamed to "
+                        "pinned host slots by spgemm_run_batched"}
     # the hybrid accumulator on the same product: CTA-tier columns whose
     # products fit their table are sorted by row instead of hashed
-    h = bench_step(spg, torch, args, A, dev, tuning=spg.Tuning(hybrid_sort=True),
+    h = bench_step(spg, torch, args, A, dev, budget=budget, tuning=spg.Tuning(hybrid_sort=True),
                    note="hybrid accumulator (sort-based for low-cf CTA-tier columns)")
     h.pop("_counts")
     r["hybrid_sort"] = {k: h[k] for k in ("value", "unit", "ms_per_step", "phase_ms_per_step", "note")}
+    if not args.no_cpu:
+        v, desc, cores, dt = cpu_oracle_sample(A, f, 4e9)
+        r["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                             "seconds": dt}
     return r
+
+
+def bench_config1(spg, torch, args, dev):
+    """Config 1: C = A*A for a 4,096^2 Erdos-Renyi matrix with exactly 8 rows
+    per column, fp64, int32 -- a latency case (the inputs fit in L2): one
+    plain single-batch symbolic + numeric, in microseconds per product."""
+    A = W.config1()
+    st = torch.cuda.current_stream()
+    Ad = spg.Csc.from_host(A, device=f"cuda:{dev}")
+    plan = spg.Plan(Ad, Ad)
+    info = plan.symbolic()
+    out = plan.alloc_batch(0)
+
+    def step():
+        plan.symbolic()
+        plan.numeric(0, out=out)
+    for _ in range(5):
+        step()
+    torch.cuda.synchronize()
+    n = 50
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(n):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) / n * 1e3
+    plan.check_errors()
+    plan.close()
+    F = int(info["flops"])
+    r = {"us_per_product": us, "value": 2 * F / (us / 1e6) / 1e9, "unit": UNIT, "flops": F,
+         "nnz_c": int(info["nnz_c"]), "nbatches": int(info["nbatches"]),
+         "note": "symbolic (one host synchronisation) + numeric; inputs fit in L2, so the HBM "
+                 "roofline does not apply"}
+    if not args.no_cpu:
+        import oracle
+        t0 = time.perf_counter()
+        for _ in range(5):
+            oracle.spgemm(A, A)
+        dt = (time.perf_counter() - t0) / 5
+        r["cpu_baseline"] = {"value": 2 * F / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "us_per_product": dt * 1e6,
+                             "sample": "the whole product, 5 runs"}
+    return r
+
+
+def bench_aat(spg, torch, args, dev):
+    """A*A^T and row-wise batching on a k-mer-like matrix (2 nonzeros per
+    column, the Rice-kmers shape the paper's A*A^T runs use): A 1,000,000 x
+    4,000,000, fp32, int32. The transpose, the product, and the row-batched
+    stream of C (column batches of C^T = A A^T, handed over as rows)."""
+    import oracle  # noqa: F401  (inputs only)
+    A = W.er_exact(1_000_000, 4_000_000, 2, W.config_seed(6), index_dtype=np.int32,
+                   value_dtype=np.float32)
+    Ad = spg.Csc.from_host(A, device=f"cuda:{dev}")
+    st = torch.cuda.current_stream()
+    spg.spgemm_aat(Ad)
+    torch.cuda.synchronize()
+    n = 3
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(n):
+        C = spg.spgemm_aat(Ad)
+        del C
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    F = 4 * A.ncols   # every column of A (2 entries) gives 4 products of A A^T
+    rows = {"blocks": 0}
+
+    def sink(batch, r0, r1, arrs):
+        rows["blocks"] += 1
+        return 0
+    At = spg.transpose(Ad)
+    budget = (A.bytes() * 6) + (256 << 20)
+    t0 = time.perf_counter()
+    spg.run_row_batched(Ad, At, sink, budget=budget, host_slot_bytes=1 << 28, host_slots=3)
+    torch.cuda.synchronize()
+    rb = time.perf_counter() - t0
+    del At, Ad
+    torch.cuda.empty_cache()
+    return {"value": 2 * F / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_product": ms, "flops": F,
+            "row_batched_ms": rb * 1e3, "row_blocks": rows["blocks"],
+            "note": "A*A^T (device transpose + product) and the same product streamed by row blocks"}
 
 
 def bench_sorted_topk(spg, torch, args, A, F, dev, topk=1000):
@@ -689,8 +882,24 @@ def bench_fwdbwd(spg, torch, args):
         plain()
     torch.cuda.synchronize()
     tp = (time.perf_counter() - t0) / reps
-    return {"fused_ms": tf * 1e3, "plain_ms": tp * 1e3, "speedup": tp / tf,
-            "note": "plain path = forward SpGEMM + two full SpGEMMs on transposes (mask not applied)"}
+    r = {"fused_ms": tf * 1e3, "plain_ms": tp * 1e3, "speedup": tp / tf,
+         "flops_forward": int(flops_host_ab(A, B).sum()),
+         "note": "plain path = forward SpGEMM + two full SpGEMMs on transposes (mask not applied); "
+                 "G = N(0,1) values on C's pattern"}
+    if not args.no_cpu:
+        import oracle
+        t0 = time.perf_counter()
+        Cr = oracle.spgemm(A, B)
+        G = W.values_on_pattern(Cr, 5, dist="normal", value_dtype=np.float32)
+        t1 = time.perf_counter()
+        oracle.backward(A, B, G)
+        t2 = time.perf_counter()
+        r["cpu_baseline"] = {"fwd_bwd_ms": (t1 - t0 + t2 - t1) * 1e3, "fwd_ms": (t1 - t0) * 1e3,
+                             "bwd_ms": (t2 - t1) * 1e3, "cores": oracle.num_threads(), "kind": "oracle",
+                             "speedup_of_fused": (t2 - t0) / tf,
+                             "sample": "the whole forward product and both gradients (the backward "
+                                       "oracle runs on one thread)"}
+    return r
 
 
 def main():
