@@ -120,6 +120,12 @@ typedef struct {
  *                  factor) is accumulated by sorting its products by row and
  *                  summing equal rows instead of hashing them (a hybrid
  *                  accumulator chosen per column); 0: hash only.
+ *   warp_max_cap   batched products (spgemm_multi_*): largest column bound
+ *                  handled by one warp with a private table (32, 128, 256 or
+ *                  512); larger columns take a whole CTA.
+ * For spgemm_multi_*, hash_max_cap is the largest shared-memory table (larger
+ * columns use a global-memory table) and block_tier_threads the CTA width of
+ * its persistent passes (256 or 512).
  */
 typedef struct {
     int hash_max_cap;
@@ -128,7 +134,8 @@ typedef struct {
     int huge_seg;
     int block_tier_threads;
     int hybrid_sort;
-    int reserved[2];
+    int warp_max_cap;
+    int reserved[1];
 } spgemm_tuning;
 
 /*

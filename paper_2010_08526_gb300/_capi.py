@@ -29,7 +29,7 @@ class SpgemmTuning(ctypes.Structure):
     _fields_ = [
         ("hash_max_cap", ctypes.c_int), ("panel_rows", ctypes.c_int), ("short_seg", ctypes.c_int),
         ("huge_seg", ctypes.c_int), ("block_tier_threads", ctypes.c_int),
-        ("hybrid_sort", ctypes.c_int), ("reserved", ctypes.c_int * 2),
+        ("hybrid_sort", ctypes.c_int), ("warp_max_cap", ctypes.c_int), ("reserved", ctypes.c_int * 1),
     ]
 
 

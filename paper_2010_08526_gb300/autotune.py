@@ -10,6 +10,12 @@ current stream and returns the fastest. The knobs:
                          size);
 * block_tier_threads  -- CTA size of the hash tiers (block shape).
 
+For the batched products (Multi) the knobs are those of its persistent
+passes: hash_max_cap (the largest shared-memory table, so the split between
+CTA items and global-table items and the shared memory each CTA holds),
+warp_max_cap (the largest column one warp takes with a private table) and
+block_tier_threads (CTA width, 256 or 512); multi_candidates() is the grid.
+
 Every candidate is checked to give the same nnz(C) as the first one; a
 candidate that fails (for example an invalid combination) is skipped.
 """
@@ -88,11 +94,25 @@ def tune_plan(A: Csc, B: Csc, cands: Optional[Iterable[Tuning]] = None, reps: in
     return best, results
 
 
+MULTI_CAPS = (1024, 2048, 4096, 8192)
+MULTI_WARP_CAPS = (128, 256, 512)
+MULTI_THREADS = (256, 512)
+
+
+def multi_candidates(caps: Sequence[int] = MULTI_CAPS, warp_caps: Sequence[int] = MULTI_WARP_CAPS,
+                     threads: Sequence[int] = MULTI_THREADS) -> List[Tuning]:
+    """The grid of the batched passes' knobs (combinations whose tables do
+    not fit are refused by the library and skipped)."""
+    return [Tuning(hash_max_cap=c, warp_max_cap=w, block_tier_threads=t)
+            for c, w, t in itertools.product(caps, warp_caps, threads) if w <= c]
+
+
 def tune_multi(As: List[Csc], Bs: List[Csc], cands: Optional[Iterable[Tuning]] = None,
                reps: int = 2) -> Tuple[Tuning, list]:
-    """The batched multi-problem pass (CUDA graph) for each candidate."""
+    """The batched multi-problem pass (CUDA graph) for each candidate; the
+    fastest Tuning and the (tuning, ms) list."""
     if cands is None:
-        cands = [Tuning(hash_max_cap=8192, block_tier_threads=t) for t in DEFAULT_THREADS]
+        cands = multi_candidates()
     results = []
     for tun in cands:
         try:

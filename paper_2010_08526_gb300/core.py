@@ -91,6 +91,7 @@ class Tuning:
     huge_seg: int = 0
     block_tier_threads: int = 0
     hybrid_sort: bool = False
+    warp_max_cap: int = 0
 
     def struct(self) -> C.SpgemmTuning:
         t = C.SpgemmTuning()
@@ -98,6 +99,7 @@ class Tuning:
         t.short_seg, t.huge_seg = self.short_seg, self.huge_seg
         t.block_tier_threads = self.block_tier_threads
         t.hybrid_sort = int(bool(self.hybrid_sort))
+        t.warp_max_cap = self.warp_max_cap
         return t
 
 

@@ -386,8 +386,8 @@ spgemm_status spgemm_backward(spgemm_plan *plan, const spgemm_csc *G, void *dA_v
 
 namespace spg {
 void MultiState::release_all() {
-    DevBuf *bufs[] = {&probs, &f, &cnt, &colptr, &tier, &list, &off, &list2, &off2, &hist,
-                      &cursor, &err, &scan_part, &rows, &vals};
+    DevBuf *bufs[] = {&probs, &f, &cnt, &colptr, &tier, &list, &off, &hist, &cursor, &err,
+                      &scan_part, &rows, &vals, &counter, &gsize, &gtab_off, &gkeys, &gvals};
     for (auto *b : bufs) b->release();
     h_small.release();
     if (exec) cudaGraphExecDestroy(exec);
@@ -539,7 +539,29 @@ spgemm_status spgemm_multi_create(int nprob, const spgemm_csc *As, const spgemm_
         if (tu->short_seg) ms.tun.short_seg = tu->short_seg;
         if (tu->huge_seg) ms.tun.huge_seg = tu->huge_seg;
         if (tu->block_tier_threads) ms.tun.block_threads = tu->block_tier_threads;
+        if (tu->warp_max_cap) {
+            static const int kWarpCaps[5] = {0, 32, 128, 256, 512};   // warp tiers 1..4
+            int wt = 0;
+            for (int t = 1; t <= 4; ++t) if (kWarpCaps[t] == tu->warp_max_cap) wt = t;
+            if (!wt) {
+                set_error("warp_max_cap must be 32, 128, 256 or 512");
+                delete mh;
+                return SPGEMM_ERR_INVALID;
+            }
+            ms.warp_tiers = wt;
+        }
     }
+    {
+        bool ok = false;
+        for (int c = 256; c <= 8192; c <<= 1) ok |= ms.tun.hash_cap_max == c;
+        static const int kWarpCaps[5] = {0, 32, 128, 256, 512};
+        if (!ok || ms.tun.hash_cap_max < kWarpCaps[ms.warp_tiers]) {
+            set_error("hash_max_cap must be a power of two from 256 to 8192, at least warp_max_cap");
+            delete mh;
+            return SPGEMM_ERR_INVALID;
+        }
+    }
+    ms.threads = ms.tun.block_threads >= 512 || ms.tun.block_threads == 0 ? 512 : 256;
     s = multi_create_typed(ms, As, Bs, stream);
     if (s != SPGEMM_OK) { ms.release_all(); delete mh; return s; }
     *out = mh;

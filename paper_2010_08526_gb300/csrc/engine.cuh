@@ -157,6 +157,10 @@ template <class I, class V> struct Engine : EngineBase {
         set_smem(k_num_heavy<SrcPartsRange<I, V>, SrcPartsRange<I, V>, 2>, mx);
         set_smem(k_num_heavy<SrcPanelRange<I, V>, SrcColRange<I, V>, 3>, mx);
         set_smem(k_num_heavy<SrcPartsRange<I, V>, SrcPartsRange<I, V>, 3>, mx);
+        set_smem(k_multi_pass<SrcGemm<I, V>, 512, 0>, mx);
+        set_smem(k_multi_pass<SrcGemm<I, V>, 512, 1>, mx);
+        set_smem(k_multi_pass<SrcGemm<I, V>, 256, 0>, mx);
+        set_smem(k_multi_pass<SrcGemm<I, V>, 256, 1>, mx);
         set_smem(k_num_heavy32<I, V, 1>, mx);
         set_smem(k_num_heavy32<I, V, 2>, mx);
         set_smem(k_sort_block<I, V, 1024>, mx);
@@ -1494,9 +1498,7 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(ms.colptr.ensure(sizeof(int64_t) * (n + 1)));
         SPG_CK(ms.tier.ensure(n + 16));
         SPG_CK(ms.list.ensure(sizeof(int32_t) * (n + 1)));
-        SPG_CK(ms.list2.ensure(sizeof(int32_t) * (n + 1)));
         SPG_CK(ms.off.ensure(sizeof(int32_t) * 64));
-        SPG_CK(ms.off2.ensure(sizeof(int32_t) * 64));
         SPG_CK(ms.hist.ensure(sizeof(int32_t) * 64));
         SPG_CK(ms.cursor.ensure(sizeof(int32_t) * 64));
         SPG_CK(ms.err.ensure(sizeof(int) * 4));
@@ -1519,17 +1521,44 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(cudaStreamSynchronize(st));
         int hist[16];
         std::memcpy(hist, ms.h_small.p, sizeof(hist));
-        for (int t = kHeavyTier0; t < kTiers; ++t)
-            if (n > 0 && hist[t]) {
-                set_error("a column of a batched problem may hold more than " +
-                          std::to_string(ms.tun.hash_cap_max) +
-                          " distinct rows; multiply that problem with a plan instead");
-                return SPGEMM_ERR_INVALID;
-            }
         ms.total_flops = *(int64_t *)(ms.h_small.as<char>() + 256);
         ms.capacity = ms.total_flops;
         SPG_CK(ms.rows.ensure(sizeof(I) * (size_t)(ms.capacity + 1)));
         SPG_CK(ms.vals.ensure(sizeof(V) * (size_t)(ms.capacity + 1)));
+        // columns above the largest shared-memory table: one global-memory
+        // hash table each (2 * min(f_j, m) slots, a power of two)
+        ms.heavy_cols = 0;
+        for (int t = kHeavyTier0; t < kTiers; ++t) ms.heavy_cols += n > 0 ? hist[t] : 0;
+        SPG_CK(ms.gtab_off.ensure(sizeof(int64_t) * (n + 1)));
+        if (ms.heavy_cols) {
+            SPG_CK(ms.gsize.ensure(sizeof(int64_t) * (n + 1)));
+            k_multi_gtab_sizes<SrcGemm<I, V>><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                multi_args(ms), ms.f.as<int64_t>(), ms.tier.as<uint8_t>(), n, ms.gsize.as<int64_t>());
+            SPG_CK(cudaGetLastError());
+            SPG_CK(exclusive_scan_i64(ms.gsize.as<int64_t>(), n, ms.gtab_off.as<int64_t>(),
+                                      ms.scan_part.as<int64_t>(), 1, st));
+            int64_t gslots = 0;
+            SPG_CK(cudaMemcpyAsync(&gslots, ms.gtab_off.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            SPG_CK(cudaStreamSynchronize(st));
+            SPG_CK(ms.gkeys.ensure(sizeof(uint32_t) * (size_t)(gslots + 1)));
+            SPG_CK(ms.gvals.ensure(sizeof(V) * (size_t)(gslots + 1)));
+        }
+        SPG_CK(ms.counter.ensure(sizeof(unsigned long long) * 2));
+        // shared memory of the persistent passes: the largest CTA table or
+        // the warps' private tables, whichever is larger
+        const size_t sv = sizeof(V) + 4;
+        const size_t nw = (size_t)ms.threads / 32;
+        ms.smem = std::max((size_t)2 * ms.tun.hash_cap_max * sv, nw * 2 * tier_cap(ms.warp_tiers) * sv);
+        int per_sm = 0;
+        cudaError_t oe = ms.threads == 512
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_pass<SrcGemm<I, V>, 512, 1>, 512, ms.smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_pass<SrcGemm<I, V>, 256, 1>, 256, ms.smem);
+        SPG_CK(oe);
+        if (per_sm < 1) {
+            set_error("the batched tables do not fit shared memory: lower hash_max_cap or warp_max_cap");
+            return SPGEMM_ERR_INVALID;
+        }
+        ms.grid = ms.nsm * per_sm;
         ms.enqueue = &multi_enqueue;
         return SPGEMM_OK;
     }
@@ -1542,28 +1571,43 @@ template <class I, class V> struct Engine : EngineBase {
         GA ga = multi_args(ms);
         SPG_CK(cudaMemsetAsync(cx.hist, 0, sizeof(int32_t) * 64, st));
         SPG_CK(cudaMemsetAsync(cx.cursor, 0, sizeof(int32_t) * 64, st));
+        SPG_CK(cudaMemsetAsync(ms.counter.p, 0, sizeof(unsigned long long) * 2, st));
         if (n > 0) {
+            // tiers by the flop bound min(f_j, m), the same as at creation
             k_flops_bin<SrcGemm<I, V>><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
                 ga, 0, n, cx.tun.hash_cap_max, nullptr, nullptr, ms.tier.as<uint8_t>(),
                 ms.cnt.as<int64_t>(), cx.hist);
             k_bin_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
                 ms.tier.as<uint8_t>(), 0, n, cx.hist, cx.cursor, ms.list.as<int32_t>(),
                 ms.off.as<int32_t>(), nullptr);
-            TierCommon c = common_of(cx);
-            c.list = ms.list.as<int32_t>(); c.list_off = ms.off.as<int32_t>();
-            c.cnt = ms.cnt.as<int64_t>();
-            for (int t = 1; t <= 8; ++t) {
-                if (tier_cap(t) > cx.tun.hash_cap_max) break;
-                launch_sym_tier<SrcGemm<I, V>>(cx, ga, c, t, -1, st);
-            }
+        }
+        TierCommon c = common_of(cx);
+        c.cnt = ms.cnt.as<int64_t>();
+        MultiQueue mq{ms.list.as<int32_t>(), ms.off.as<int32_t>(), ms.counter.as<unsigned long long>(),
+                      ms.gtab_off.as<int64_t>(), ms.gkeys.as<uint32_t>(), ms.gvals.p, ms.warp_tiers};
+        // one persistent launch counts every column of every problem ...
+        if (n > 0) {
+            if (ms.threads == 512)
+                k_multi_pass<SrcGemm<I, V>, 512, 0><<<ms.grid, 512, ms.smem, st>>>(ga, c, mq, nullptr, nullptr);
+            else
+                k_multi_pass<SrcGemm<I, V>, 256, 0><<<ms.grid, 256, ms.smem, st>>>(ga, c, mq, nullptr, nullptr);
         }
         SPG_CK(cudaGetLastError());
         SPG_CK(exclusive_scan_i64(ms.cnt.as<int64_t>(), n, ms.colptr.as<int64_t>(),
                                   ms.scan_part.as<int64_t>(), 1, st));
-        NumOut<I, V> o{ms.colptr.as<int64_t>(), 0, ms.rows.as<I>(), ms.vals.as<V>()};
-        SPG_ST((num_pass<SrcGemm<I, V>, SrcPanel<I, V>>(
-            cx, ga, ga, 0, n, ms.cnt.as<int64_t>(), nullptr, o, nullptr, false, nullptr, nullptr,
-            nullptr, nullptr, ms.tier.as<uint8_t>(), ms.list2.as<int32_t>(), ms.off2.as<int32_t>(), st)));
+        // ... and one forms them, into the output arena at the scanned offsets
+        c.colptr = ms.colptr.as<int64_t>();
+        c.out_base = 0;
+        mq.counter = ms.counter.as<unsigned long long>() + 1;
+        if (n > 0) {
+            if (ms.threads == 512)
+                k_multi_pass<SrcGemm<I, V>, 512, 1><<<ms.grid, 512, ms.smem, st>>>(ga, c, mq, ms.rows.as<I>(),
+                                                                                    ms.vals.as<V>());
+            else
+                k_multi_pass<SrcGemm<I, V>, 256, 1><<<ms.grid, 256, ms.smem, st>>>(ga, c, mq, ms.rows.as<I>(),
+                                                                                    ms.vals.as<V>());
+        }
+        SPG_CK(cudaGetLastError());
         return SPGEMM_OK;
     }
 };

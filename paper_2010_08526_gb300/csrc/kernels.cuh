@@ -1736,3 +1736,4 @@ template <class V> __global__ void k_fill_zero(V *p, int64_t n) {
 }  // namespace spg
 
 #include "dense_items.cuh"
+#include "multi_persistent.cuh"

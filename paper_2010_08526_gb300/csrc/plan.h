@@ -283,10 +283,16 @@ struct MultiState {
     int nprob = 0, idx64 = 0, vtype = 0, nsm = 148;
     AllocFns alloc;          // workspace allocator (opts->allocator, copied)
     Tuning tun;
-    DevBuf probs, f, cnt, colptr, tier, list, off, list2, off2, hist, cursor, err, scan_part;
+    DevBuf probs, f, cnt, colptr, tier, list, off, hist, cursor, err, scan_part;
     DevBuf rows, vals;
+    DevBuf counter;                // work-item counters of the two persistent passes
+    DevBuf gsize, gtab_off, gkeys, gvals;   // global tables of the heavy columns
     HostBuf h_small;
-    int64_t total_cols = 0, capacity = 0, total_flops = 0;
+    int64_t total_cols = 0, capacity = 0, total_flops = 0, heavy_cols = 0;
+    int warp_tiers = 4;            // tiers 1..warp_tiers run one warp per column
+    int threads = 512;             // CTA width of the persistent passes
+    int grid = 0;                  // resident CTAs of the persistent passes
+    size_t smem = 0;               // their dynamic shared memory
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t own = nullptr;

@@ -624,24 +624,52 @@ def test_autotuner_picks_a_working_candidate():
 
 # ---------------------------------------------------------------- batched problems
 
-def test_multi_path_counting_exact():
-    probs = W.config4(count=24, nmax=5000)
+def _check_multi(probs, Bs=None, **kw):
+    Bs = Bs if Bs is not None else probs
     dev = [to_dev(p) for p in probs]
+    devb = dev if Bs is probs else [to_dev(b) for b in Bs]
     for use_graph in (False, True):
-        M = spg.Multi(dev, dev)
+        M = spg.Multi(dev, devb, **kw)
         M.run(use_graph=use_graph)
         M.run(use_graph=use_graph)   # replay
         torch.cuda.synchronize()
         cp, ri, va = M.output()
         cp = cp.cpu().numpy(); ri = ri.cpu().numpy(); va = va.cpu().numpy()
         col = 0
-        for p in probs:
-            ref = oracle.spgemm(p, p)
-            a, b = cp[col], cp[col + p.ncols]
-            got = CSC(p.nrows, p.ncols, cp[col:col + p.ncols + 1] - a, ri[a:b].astype(np.int64), va[a:b])
+        for p, b in zip(probs, Bs):
+            ref = oracle.spgemm(p, b)
+            lo, hi = cp[col], cp[col + b.ncols]
+            got = CSC(p.nrows, b.ncols, cp[col:col + b.ncols + 1] - lo, ri[lo:hi].astype(np.int64), va[lo:hi])
             assert_matches(got, ref, exact=True, label="multi")
-            col += p.ncols
+            col += b.ncols
         M.close()
+
+
+def test_multi_path_counting_exact():
+    _check_multi(W.config4(count=24, nmax=5000))
+
+
+@pytest.mark.parametrize("tun", [dict(hash_max_cap=1024, warp_max_cap=128, block_tier_threads=256),
+                                 dict(hash_max_cap=4096, warp_max_cap=32, block_tier_threads=512),
+                                 dict(hash_max_cap=8192, warp_max_cap=512, block_tier_threads=512)])
+def test_multi_tuning_variants(tun):
+    _check_multi(W.config4(count=16, nmax=8000), tuning=spg.Tuning(**tun))
+
+
+def test_multi_heavy_columns_use_global_tables():
+    """Problems with hub columns above the largest shared-memory table (the
+    refusal of earlier versions): their columns take global-memory tables in
+    the same persistent launch as the small ones. int64 path counts, exact."""
+    probs = W.config4(count=6, nmax=3000)
+    hubs = [skewed(5000, 5000, 900 + i, hubs=2, hub_deg=3000, base=3, dist="ones") for i in range(3)]
+    allp = probs[:3] + hubs + probs[3:]
+    _check_multi(allp, tuning=spg.Tuning(hash_max_cap=1024))
+    # rectangular problems with heavy columns and an empty one
+    A1 = skewed(4000, 300, 911, hubs=1, hub_deg=3500, base=4, dist="ones")
+    B1 = skewed(300, 700, 912, hubs=2, hub_deg=250, base=8, dist="ones")
+    Z = CSC(50, 40, np.zeros(41, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64))
+    Zb = CSC(40, 30, np.zeros(31, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64))
+    _check_multi([A1, Z] + probs[:2], Bs=[B1, Zb] + probs[:2], tuning=spg.Tuning(hash_max_cap=256, warp_max_cap=128))
 
 
 # ------------------------------------------------------ every output slot written
