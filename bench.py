@@ -312,7 +312,7 @@ def run_gpu(args):
     achieved = bytes_per_launch / (dense_ms / 1e3) / 1e9 if dense_ms > 0 else 0.0
     phase_ms = {k: round(v / args.steps, 3) for k, v in stats["ms"].items() if v}
     traffic = None
-    tf = os.path.join(ROOT, "profiles", "traffic_num_heavy.txt")
+    tf = os.path.join(ROOT, "profiles", "traffic_num_heavy32.txt")
     if os.path.exists(tf) and args.scale == 20:
         for line in open(tf):
             if line.startswith("bytes_per_full_launch"):
@@ -453,7 +453,7 @@ def run_gpu(args):
                        "nbatches": info["nbatches"], "budget": "80% of free HBM",
                        "l2": "inputs and outputs larger than L2 (no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-            "roofline": {"bound": "hbm", "kernel": "k_num_heavy (heavy-column numeric: dense row panels + hash row ranges)",
+            "roofline": {"bound": "hbm", "kernel": "k_num_heavy32 (heavy-column numeric: dense row panels + hash row ranges)",
                          "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
                          "algorithmic_bytes_per_launch": bytes_per_launch,

@@ -122,10 +122,10 @@ typedef struct {
  *                  accumulator chosen per column); 0: hash only.
  *   warp_max_cap   batched products (spgemm_multi_*): largest column bound
  *                  handled by one warp with a private table (32, 128, 256 or
- *                  512); larger columns take a whole CTA.
+ *                  512; default 256); larger columns take a whole CTA.
  * For spgemm_multi_*, hash_max_cap is the largest shared-memory table (larger
- * columns use a global-memory table) and block_tier_threads the CTA width of
- * its persistent passes (256 or 512).
+ * columns use a global-memory table; default 1024) and block_tier_threads the
+ * CTA width of its persistent passes (128, 256 or 512; default 128).
  */
 typedef struct {
     int hash_max_cap;

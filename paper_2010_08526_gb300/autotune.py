@@ -14,7 +14,7 @@ For the batched products (Multi) the knobs are those of its persistent
 passes: hash_max_cap (the largest shared-memory table, so the split between
 CTA items and global-table items and the shared memory each CTA holds),
 warp_max_cap (the largest column one warp takes with a private table) and
-block_tier_threads (CTA width, 256 or 512); multi_candidates() is the grid.
+block_tier_threads (CTA width, 128, 256 or 512); multi_candidates() is the grid.
 
 Every candidate is checked to give the same nnz(C) as the first one; a
 candidate that fails (for example an invalid combination) is skipped.
@@ -96,7 +96,7 @@ def tune_plan(A: Csc, B: Csc, cands: Optional[Iterable[Tuning]] = None, reps: in
 
 MULTI_CAPS = (1024, 2048, 4096, 8192)
 MULTI_WARP_CAPS = (128, 256, 512)
-MULTI_THREADS = (256, 512)
+MULTI_THREADS = (128, 256, 512)
 
 
 def multi_candidates(caps: Sequence[int] = MULTI_CAPS, warp_caps: Sequence[int] = MULTI_WARP_CAPS,

@@ -533,6 +533,10 @@ spgemm_status spgemm_multi_create(int nprob, const spgemm_csc *As, const spgemm_
     ms.idx64 = As[0].idx_type == SPGEMM_I64;
     ms.vtype = As[0].val_type;
     ms.nsm = prop.multiProcessorCount;
+    // defaults of the persistent passes: small shared tables and 128-thread
+    // CTAs keep many CTAs resident per SM (batched problems are mostly small)
+    ms.tun.hash_cap_max = 1024;
+    ms.warp_tiers = 3;   // warp tables up to 256 rows
     if (opts && opts->tuning) {
         const spgemm_tuning *tu = opts->tuning;
         if (tu->hash_max_cap) ms.tun.hash_cap_max = tu->hash_max_cap;
@@ -561,7 +565,8 @@ spgemm_status spgemm_multi_create(int nprob, const spgemm_csc *As, const spgemm_
             return SPGEMM_ERR_INVALID;
         }
     }
-    ms.threads = ms.tun.block_threads >= 512 || ms.tun.block_threads == 0 ? 512 : 256;
+    ms.threads = ms.tun.block_threads == 0 ? 128 : ms.tun.block_threads >= 512 ? 512
+                 : ms.tun.block_threads >= 256 ? 256 : 128;
     s = multi_create_typed(ms, As, Bs, stream);
     if (s != SPGEMM_OK) { ms.release_all(); delete mh; return s; }
     *out = mh;

@@ -161,6 +161,8 @@ template <class I, class V> struct Engine : EngineBase {
         set_smem(k_multi_pass<SrcGemm<I, V>, 512, 1>, mx);
         set_smem(k_multi_pass<SrcGemm<I, V>, 256, 0>, mx);
         set_smem(k_multi_pass<SrcGemm<I, V>, 256, 1>, mx);
+        set_smem(k_multi_pass<SrcGemm<I, V>, 128, 0>, mx);
+        set_smem(k_multi_pass<SrcGemm<I, V>, 128, 1>, mx);
         set_smem(k_num_heavy32<I, V, 1>, mx);
         set_smem(k_num_heavy32<I, V, 2>, mx);
         set_smem(k_sort_block<I, V, 1024>, mx);
@@ -263,11 +265,13 @@ template <class I, class V> struct Engine : EngineBase {
     // Cut the heavy columns of the symbolic list into work items (dense
     // panels and hash ranges) from their per-panel output counts; reads the
     // item total back (one small synchronisation).
+    // max_panels: panels one hash item may span (any number for the products;
+    // kRangeMaxPanels when the items are later sorted, or merged part by part)
     static spgemm_status build_items(const Ctx &cx, int nheavy, const int32_t *sym_list,
                                      const int32_t *sym_off, const int64_t *sel,
                                      const int32_t *pcnt, int64_t n, DevBuf &items, DevBuf &icnt,
                                      DevBuf &ioff, DevBuf &scan_part, DevBuf &order,
-                                     int64_t *n_items, cudaStream_t st) {
+                                     int64_t *n_items, cudaStream_t st, int max_panels = kRangeMaxPanels) {
         *n_items = 0;
         if (!nheavy) return SPGEMM_OK;
         SPG_CK(icnt.ensure(sizeof(int64_t) * (nheavy + 1)));
@@ -281,7 +285,7 @@ template <class I, class V> struct Engine : EngineBase {
         const int dmin = std::max(1, std::min(R / 8, rcap));
         const unsigned nb = (unsigned)((nheavy + 255) / 256);
         k_heavy_items<<<nb, 256, 0, st>>>(sym_list, sym_off, sel, cx.tun.hash_cap_max, 0, n, pcnt, cx.P,
-                                          dmin, rcap, 0, icnt.as<int64_t>(), nullptr, nullptr);
+                                          dmin, rcap, max_panels, 0, icnt.as<int64_t>(), nullptr, nullptr);
         SPG_CK(exclusive_scan_i64(icnt.as<int64_t>(), nheavy, ioff.as<int64_t>(),
                                   scan_part.as<int64_t>(), 1, st));
         int64_t total = 0;
@@ -291,7 +295,7 @@ template <class I, class V> struct Engine : EngineBase {
         std::memcpy(&total, cx.h_small + 256, sizeof(int64_t));
         SPG_CK(items.ensure(sizeof(HeavyItem) * (size_t)(total + 1)));
         k_heavy_items<<<nb, 256, 0, st>>>(sym_list, sym_off, sel, cx.tun.hash_cap_max, 0, n, pcnt, cx.P,
-                                          dmin, rcap, 1, nullptr, ioff.as<int64_t>(), items.as<HeavyItem>());
+                                          dmin, rcap, max_panels, 1, nullptr, ioff.as<int64_t>(), items.as<HeavyItem>());
         // panel-major processing order: item indices sorted by first panel,
         // stored after the items (icnt is reused for the panel histogram)
         SPG_CK(order.ensure(sizeof(int32_t) * (size_t)(total + 1)));
@@ -606,9 +610,14 @@ template <class I, class V> struct Engine : EngineBase {
         SPG_CK(cudaMemcpyAsync(ps.h_small.as<char>() + 512, ps.wbytes.as<int64_t>() + n, sizeof(int64_t),
                                cudaMemcpyDeviceToHost, st));
         if (ps.nheavy) SPG_ST(build_panels(ps, st));
+        // products alone: a hash item may span any number of panels (one run
+        // of the column-grouped copy of A); sorted output and the k-split's
+        // part-by-part merges keep the narrower items
+        const int max_panels = (ps.opts.sort_output || ps.s > 1 || !ps.A.nnz || ps.A.nnz >= (int64_t(1) << 31))
+                                   ? kRangeMaxPanels : std::max(kRangeMaxPanels, ps.P);
         SPG_ST(build_items(cx, ps.nheavy, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                            ps.cnt.as<int64_t>(), ps.pcnt.as<int32_t>(), n, ps.items, ps.item_cnt,
-                           ps.item_off, ps.scan_part, ps.item_order, &ps.n_items, st));
+                           ps.item_off, ps.scan_part, ps.item_order, &ps.n_items, st, max_panels));
         SPG_CK(cudaStreamSynchronize(st));
         const int errw = *(int *)(ps.h_small.as<char>() + 256);
         if (errw) {
@@ -1543,7 +1552,7 @@ template <class I, class V> struct Engine : EngineBase {
             SPG_CK(ms.gkeys.ensure(sizeof(uint32_t) * (size_t)(gslots + 1)));
             SPG_CK(ms.gvals.ensure(sizeof(V) * (size_t)(gslots + 1)));
         }
-        SPG_CK(ms.counter.ensure(sizeof(unsigned long long) * 2));
+        SPG_CK(ms.counter.ensure(sizeof(unsigned long long) * 4));
         // shared memory of the persistent passes: the largest CTA table or
         // the warps' private tables, whichever is larger
         const size_t sv = sizeof(V) + 4;
@@ -1552,7 +1561,9 @@ template <class I, class V> struct Engine : EngineBase {
         int per_sm = 0;
         cudaError_t oe = ms.threads == 512
             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_pass<SrcGemm<I, V>, 512, 1>, 512, ms.smem)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_pass<SrcGemm<I, V>, 256, 1>, 256, ms.smem);
+            : ms.threads == 256
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_pass<SrcGemm<I, V>, 256, 1>, 256, ms.smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_pass<SrcGemm<I, V>, 128, 1>, 128, ms.smem);
         SPG_CK(oe);
         if (per_sm < 1) {
             set_error("the batched tables do not fit shared memory: lower hash_max_cap or warp_max_cap");
@@ -1571,7 +1582,7 @@ template <class I, class V> struct Engine : EngineBase {
         GA ga = multi_args(ms);
         SPG_CK(cudaMemsetAsync(cx.hist, 0, sizeof(int32_t) * 64, st));
         SPG_CK(cudaMemsetAsync(cx.cursor, 0, sizeof(int32_t) * 64, st));
-        SPG_CK(cudaMemsetAsync(ms.counter.p, 0, sizeof(unsigned long long) * 2, st));
+        SPG_CK(cudaMemsetAsync(ms.counter.p, 0, sizeof(unsigned long long) * 4, st));
         if (n > 0) {
             // tiers by the flop bound min(f_j, m), the same as at creation
             k_flops_bin<SrcGemm<I, V>><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
@@ -1589,8 +1600,10 @@ template <class I, class V> struct Engine : EngineBase {
         if (n > 0) {
             if (ms.threads == 512)
                 k_multi_pass<SrcGemm<I, V>, 512, 0><<<ms.grid, 512, ms.smem, st>>>(ga, c, mq, nullptr, nullptr);
-            else
+            else if (ms.threads == 256)
                 k_multi_pass<SrcGemm<I, V>, 256, 0><<<ms.grid, 256, ms.smem, st>>>(ga, c, mq, nullptr, nullptr);
+            else
+                k_multi_pass<SrcGemm<I, V>, 128, 0><<<ms.grid, 128, ms.smem, st>>>(ga, c, mq, nullptr, nullptr);
         }
         SPG_CK(cudaGetLastError());
         SPG_CK(exclusive_scan_i64(ms.cnt.as<int64_t>(), n, ms.colptr.as<int64_t>(),
@@ -1598,13 +1611,16 @@ template <class I, class V> struct Engine : EngineBase {
         // ... and one forms them, into the output arena at the scanned offsets
         c.colptr = ms.colptr.as<int64_t>();
         c.out_base = 0;
-        mq.counter = ms.counter.as<unsigned long long>() + 1;
+        mq.counter = ms.counter.as<unsigned long long>() + 2;
         if (n > 0) {
             if (ms.threads == 512)
                 k_multi_pass<SrcGemm<I, V>, 512, 1><<<ms.grid, 512, ms.smem, st>>>(ga, c, mq, ms.rows.as<I>(),
                                                                                     ms.vals.as<V>());
-            else
+            else if (ms.threads == 256)
                 k_multi_pass<SrcGemm<I, V>, 256, 1><<<ms.grid, 256, ms.smem, st>>>(ga, c, mq, ms.rows.as<I>(),
+                                                                                    ms.vals.as<V>());
+            else
+                k_multi_pass<SrcGemm<I, V>, 128, 1><<<ms.grid, 128, ms.smem, st>>>(ga, c, mq, ms.rows.as<I>(),
                                                                                     ms.vals.as<V>());
         }
         SPG_CK(cudaGetLastError());

@@ -1169,12 +1169,12 @@ __global__ void __launch_bounds__(512, 2) k_num_dense(typename DSrc::Args sa, Ti
 // counts are cut, in panel order, into items: a panel holding at least
 // dense_min rows becomes a dense item (shared-memory accumulator over its
 // 2^log2R rows); runs of lighter panels are grouped into hash items of at most
-// kRangeCap output rows and kRangeMaxPanels panels (shared-memory hash table
+// kRangeCap output rows and a bounded number of panels (shared-memory hash table
 // keyed by the global row). Items of one column write consecutive, disjoint
 // ranges of the column's output, in panel order.
 // ---------------------------------------------------------------------------
 constexpr int kRangeCap = 8192;
-constexpr int kRangeMaxPanels = 16;
+constexpr int kRangeMaxPanels = 16;   // panels per hash item when the items are sorted or merged
 constexpr int kRangeLog2T = 14;   // 16384 slots = 2 * kRangeCap
 
 struct HeavyItem {
@@ -1190,8 +1190,8 @@ struct HeavyItem {
 // item_off[h] (exclusive scan of the counts).
 __global__ void k_heavy_items(const int32_t *list, const int32_t *list_off, const int64_t *sel,
                               int hash_cap_max, int64_t c_lo, int64_t c_hi, const int32_t *pcnt,
-                              int P, int dense_min, int range_cap, int mode, int64_t *ncount,
-                              const int64_t *item_off, HeavyItem *items);
+                              int P, int dense_min, int range_cap, int max_panels, int mode,
+                              int64_t *ncount, const int64_t *item_off, HeavyItem *items);
 
 // Panel-major item order (defined in util_kernels.cu).
 __global__ void k_items_by_panel(const HeavyItem *items, const int64_t *n_items_p, int mode,

@@ -3,12 +3,13 @@
 // formula): the symbolic count and the numeric hash accumulation of every
 // column of every problem run as work items of a single kernel.
 //
-// Work items come from the tier lists of k_bin_scatter (list, off[t]), in
-// this order: the columns above the largest shared-memory table (heaviest
-// tier first), then the CTA-sized columns (largest first), one per item;
-// then the warp-sized columns, one per warp, a group of NT/32 per item. CTAs
-// take items from a device counter (atomicAdd), so uneven problems balance
-// across SMs without a host round trip.
+// Work comes from the tier lists of k_bin_scatter (list, off[t]) through two
+// device counters. First the CTA items: the columns above the largest
+// shared-memory table (heaviest tier first), then the CTA-sized columns
+// (largest first), one per item, taken by whole CTAs (atomicAdd on the first
+// counter). Then the warp-sized columns: every warp takes a few columns at
+// a time from the second counter, with no barrier between warps. Uneven
+// problems so balance across SMs without a host round trip.
 //
 //   CTA item   : a hash table of 2 * cap(tier) slots in shared memory;
 //   warp item  : a warp-private table of 2 * cap(tier) <= 2 * 512 slots;
@@ -21,7 +22,7 @@ namespace spg {
 struct MultiQueue {
     const int32_t *list;            // global column ids grouped by tier
     const int32_t *off;             // [kTiers + 1] tier offsets in list
-    unsigned long long *counter;    // next work item (zeroed before each launch)
+    unsigned long long *counter;    // [0] next CTA item, [1] next warp column (zeroed before each launch)
     const int64_t *gtab_off;        // heavy columns: first slot of the global table
     uint32_t *gkeys;                // global tables: keys
     void *gvals;                    // global tables: values
@@ -67,15 +68,14 @@ __global__ void __launch_bounds__(NT) k_multi_pass(typename Src::Args sa, TierCo
     const int nbig = mq.off[kTiers] - mq.off[wt + 1];
     const int nwarp = mq.off[wt + 1] - mq.off[1];
     const int TW = 2 * tier_cap(wt);   // slots of the largest warp table
-    const long long nitems = (long long)nbig + (nwarp + NW - 1) / NW;
     if (threadIdx.x == 0) sh.pos = 0;
     for (;;) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(mq.counter, 1ull);
         __syncthreads();
         const long long item = s_item;
         __syncthreads();
-        if (item >= nitems) break;
-        if (item < nbig) {
+        if (item >= nbig) break;
+        {
             // one column per CTA, heaviest first (the list is ascending in tier)
             const int64_t g = mq.list[mq.off[kTiers] - 1 - item];
             Src src;
@@ -201,58 +201,63 @@ __global__ void __launch_bounds__(NT) k_multi_pass(typename Src::Args sa, TierCo
                 }
                 __syncthreads();
             }
-        } else {
-            // warp-sized columns: one per warp, warp-private tables
-            const int64_t gi = (item - nbig) * NW + warp;
-            if (gi < nwarp) {
-                const int pos = mq.off[1] + (int)gi;
-                const int64_t g = mq.list[pos];
-                int t = 1;
-                while (t < wt && mq.off[t + 1] <= pos) ++t;
-                int log2T = 1;   // 2 * cap(t) slots
-                while ((1 << log2T) < 2 * tier_cap(t)) ++log2T;
-                const int T = 1 << log2T;
-                V *vals = reinterpret_cast<V *>(smem) + warp * TW;
-                uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * NW * TW) + warp * TW;
-                Src src;
-                src.open(sa, g);
-                for (int s = lane; s < T; s += 32) { keys[s] = kEmpty; if (MODE == 1) vals[s] = V(0); }
-                __syncwarp();
-                int mine = 0;
-                auto emit = [&](int64_t q, V bv, int64_t) {
-                    bool nw;
-                    const int h = hash_insert(keys, log2T, src.row(q), nw, c.err);
-                    if (MODE == 0) mine += nw;
-                    else if (h >= 0) atomic_add_v(&vals[h], src.val(q, bv));
-                };
-                warp_walk_all(src, emit, c.short_seg);
-                __syncwarp();
-                if (MODE == 0) {
-                    mine = warp_sum(mine);
-                    if (lane == 0) c.cnt[g] = mine;
-                } else {
-                    const int64_t out0 = c.colptr[g] - c.out_base;
-                    const int64_t want = c.colptr[g + 1] - c.colptr[g];
-                    int pos2 = 0;
-                    for (int s0 = 0; s0 < T; s0 += 32) {
-                        const int s = s0 + lane;
-                        const uint32_t key = keys[s];
-                        const bool occ = key != kEmpty;
-                        const unsigned bal = __ballot_sync(SPG_FULL, occ);
-                        if (occ) {
-                            const int r = pos2 + __popc(bal & ((1u << lane) - 1u));
-                            if (r < want) {
-                                out_rows[out0 + r] = (I)key;
-                                out_vals[out0 + r] = vals[s];
-                            }
+        }
+    }
+    // warp-sized columns: every warp takes kWarpGrab at a time (one counter
+    // update per grab), each with a warp-private table
+    constexpr int kWarpGrab = 8;
+    for (;;) {
+        long long wb = 0;
+        if (lane == 0) wb = (long long)atomicAdd(mq.counter + 1, (unsigned long long)kWarpGrab);
+        wb = __shfl_sync(SPG_FULL, wb, 0);
+        if (wb >= nwarp) break;
+        for (long long wi = wb; wi < wb + kWarpGrab && wi < nwarp; ++wi) {
+            const int pos = mq.off[1] + (int)wi;
+            const int64_t g = mq.list[pos];
+            int t = 1;
+            while (t < wt && mq.off[t + 1] <= pos) ++t;
+            int log2T = 1;   // 2 * cap(t) slots
+            while ((1 << log2T) < 2 * tier_cap(t)) ++log2T;
+            const int T = 1 << log2T;
+            V *vals = reinterpret_cast<V *>(smem) + warp * TW;
+            uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * NW * TW) + warp * TW;
+            Src src;
+            src.open(sa, g);
+            for (int s = lane; s < T; s += 32) { keys[s] = kEmpty; if (MODE == 1) vals[s] = V(0); }
+            __syncwarp();
+            int mine = 0;
+            auto emit = [&](int64_t q, V bv, int64_t) {
+                bool nw;
+                const int h = hash_insert(keys, log2T, src.row(q), nw, c.err);
+                if (MODE == 0) mine += nw;
+                else if (h >= 0) atomic_add_v(&vals[h], src.val(q, bv));
+            };
+            warp_walk_all(src, emit, c.short_seg);
+            __syncwarp();
+            if (MODE == 0) {
+                mine = warp_sum(mine);
+                if (lane == 0) c.cnt[g] = mine;
+            } else {
+                const int64_t out0 = c.colptr[g] - c.out_base;
+                const int64_t want = c.colptr[g + 1] - c.colptr[g];
+                int pos2 = 0;
+                for (int s0 = 0; s0 < T; s0 += 32) {
+                    const int s = s0 + lane;
+                    const uint32_t key = keys[s];
+                    const bool occ = key != kEmpty;
+                    const unsigned bal = __ballot_sync(SPG_FULL, occ);
+                    if (occ) {
+                        const int r = pos2 + __popc(bal & ((1u << lane) - 1u));
+                        if (r < want) {
+                            out_rows[out0 + r] = (I)key;
+                            out_vals[out0 + r] = vals[s];
                         }
-                        pos2 += __popc(bal);
                     }
-                    if (lane == 0 && pos2 != want) atomicOr(c.err, kErrCount);
+                    pos2 += __popc(bal);
                 }
-                __syncwarp();
+                if (lane == 0 && pos2 != want) atomicOr(c.err, kErrCount);
             }
-            __syncthreads();
+            __syncwarp();
         }
     }
 }

@@ -285,7 +285,7 @@ struct MultiState {
     Tuning tun;
     DevBuf probs, f, cnt, colptr, tier, list, off, hist, cursor, err, scan_part;
     DevBuf rows, vals;
-    DevBuf counter;                // work-item counters of the two persistent passes
+    DevBuf counter;                // work counters of the two persistent passes (2 each)
     DevBuf gsize, gtab_off, gkeys, gvals;   // global tables of the heavy columns
     HostBuf h_small;
     int64_t total_cols = 0, capacity = 0, total_flops = 0, heavy_cols = 0;

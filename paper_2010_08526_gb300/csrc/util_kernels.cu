@@ -69,8 +69,8 @@ __global__ void k_bin_scatter(const uint8_t *tier, int64_t c_lo, int64_t c_hi,
 // the greedy cut over its P panel counts.
 __global__ void k_heavy_items(const int32_t *list, const int32_t *list_off, const int64_t *sel,
                               int hash_cap_max, int64_t c_lo, int64_t c_hi, const int32_t *pcnt,
-                              int P, int dense_min, int range_cap, int mode, int64_t *ncount,
-                              const int64_t *item_off, HeavyItem *items) {
+                              int P, int dense_min, int range_cap, int max_panels, int mode,
+                              int64_t *ncount, const int64_t *item_off, HeavyItem *items) {
     const int lo = list_off[kHeavyTier0], hi = list_off[kTiers];
     const int nh = hi - lo;
     const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,7 +97,7 @@ __global__ void k_heavy_items(const int32_t *list, const int32_t *list_off, cons
                 off += x;
                 continue;
             }
-            if (gp0 >= 0 && (gcnt + x > range_cap || p - gp0 >= kRangeMaxPanels)) flush(p);
+            if (gp0 >= 0 && (gcnt + x > range_cap || p - gp0 >= max_panels)) flush(p);
             if (x == 0 && gp0 < 0) continue;      // no open group: skip empty panels
             if (gp0 < 0) { gp0 = p; goff = off; }
             gcnt += x;
