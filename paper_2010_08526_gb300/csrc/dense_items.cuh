@@ -24,7 +24,7 @@
 // accumulator differs from the identity V(0). The item's exact row count (the
 // symbolic step's per-panel count) checks this: if fewer rows qualify (a sum
 // that cancelled back to the identity, or products equal to it), a second
-// walk marks the rows reached in a byte array and the flags decide. The
+// walk marks the rows reached in a bitmap and the bits decide. The
 // output is written one row per lane, rows ascending within the panel.
 #pragma once
 
@@ -97,11 +97,13 @@ __global__ void __launch_bounds__(kDenseChunk, MINB)
                   const int64_t *nitems_p, I *out_rows, V *out_vals) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = 1 << c.log2R;
-    // dense view: acc[R] + flg[R]; hash view (the same memory): tv[Ti] + tk[Ti]
+    // dense view: acc[R] + a presence bitmap fb[R/32] (used only when the
+    // values cannot tell presence); hash view (inside acc): tv[Ti] + tk[Ti]
     V *acc = reinterpret_cast<V *>(smem);
-    unsigned char *flg = smem + sizeof(V) * R;
+    uint32_t *fb = reinterpret_cast<uint32_t *>(smem + sizeof(V) * R);
     __shared__ DenseShared<V> sh;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) { acc[r] = V(0); flg[r] = 0; }
+    for (int r = threadIdx.x; r < R; r += blockDim.x) acc[r] = V(0);
+    for (int w = threadIdx.x; w < (R >> 5); w += blockDim.x) fb[w] = 0u;
     __syncthreads();
     const ProbDev<I, V> *pd = ga.probs;
     const I *bp = pd->bp;
@@ -269,7 +271,10 @@ __global__ void __launch_bounds__(kDenseChunk, MINB)
                         if (mode == 1) {
 #pragma unroll
                             for (int u = 0; u < kDenseBatch; ++u)
-                                if (ok[u]) flg[__ldg(&prow[q[u]])] = 1;
+                                if (ok[u]) {
+                                    const uint32_t r = __ldg(&prow[q[u]]);
+                                    atomicOr(&fb[r >> 5], 1u << (r & 31));
+                                }
                         } else if (dense) {
                             uint32_t r[kDenseBatch];
                             V x[kDenseBatch];
@@ -343,14 +348,14 @@ __global__ void __launch_bounds__(kDenseChunk, MINB)
         // A row is present when its accumulator left the identity. The
         // symbolic count of the item is exact: when fewer rows qualify (a
         // sum that cancelled to the identity, or products equal to it), the
-        // rows reached are marked in a second walk and the flags decide.
+        // rows reached are marked in a second walk and the bits decide.
         int tot;
         int o = warp_offset_total(count_touched(acc, rlo, rpw), sh.red_cnt, warp, nw, lane, tot);
         const bool by_flags = tot != mycnt;   // the same for the whole CTA
         if (by_flags) {
             walk_item(1);
             int n = 0;
-            for (int rr = rlo + lane; rr < rlo + rpw; rr += 32) n += flg[rr];
+            for (int w = (rlo >> 5) + lane; w < ((rlo + rpw) >> 5); w += 32) n += __popc(fb[w]);
             n = warp_sum(n);
             o = warp_offset_total(n, sh.red_cnt, warp, nw, lane, tot);
             if (threadIdx.x == 0 && tot != mycnt) atomicOr(c.err, kErrCount);
@@ -360,7 +365,7 @@ __global__ void __launch_bounds__(kDenseChunk, MINB)
         for (int r0 = rlo; r0 < rlo + rpw; r0 += 32) {
             const int rr = r0 + lane;
             const V a = acc[rr];
-            const bool pr = by_flags ? flg[rr] != 0 : !is_identity(a);
+            const bool pr = by_flags ? ((fb[rr >> 5] >> (rr & 31)) & 1u) != 0 : !is_identity(a);
             const unsigned bal = __ballot_sync(SPG_FULL, pr);
             if (pr) {
                 const int oo = o + __popc(bal & below_mask);
@@ -370,8 +375,11 @@ __global__ void __launch_bounds__(kDenseChunk, MINB)
                 }
                 acc[rr] = V(0);
             }
-            if (by_flags) flg[rr] = 0;
             o += __popc(bal);
+        }
+        if (by_flags) {
+            __syncwarp();
+            for (int w = (rlo >> 5) + lane; w < ((rlo + rpw) >> 5); w += 32) fb[w] = 0u;
         }
         __syncthreads();
     }

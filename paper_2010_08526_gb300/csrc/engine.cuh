@@ -165,6 +165,7 @@ template <class I, class V> struct Engine : EngineBase {
         set_smem(k_multi_pass<SrcGemm<I, V>, 128, 1>, mx);
         set_smem(k_num_heavy32<I, V, 1>, mx);
         set_smem(k_num_heavy32<I, V, 2>, mx);
+        set_smem(k_num_heavy32<I, V, 3>, mx);
         set_smem(k_sort_block<I, V, 1024>, mx);
         set_smem(k_sort_block<I, V, 8192>, mx);
         set_smem(k_sort_items<I, V, 8192>, mx);
@@ -245,6 +246,12 @@ template <class I, class V> struct Engine : EngineBase {
     static int dense_smem(const Ctx &cx) {
         const int R = 1 << cx.tun.log2R;
         return R * (int)sizeof(V) + R;
+    }
+
+    // k_num_heavy32: the accumulator and a presence bitmap
+    static int heavy32_smem(const Ctx &cx) {
+        const int R = 1 << cx.tun.log2R;
+        return R * (int)sizeof(V) + R / 8;
     }
 
     // largest hash-range item (output rows) whose table (2x slots) fits the
@@ -434,12 +441,17 @@ template <class I, class V> struct Engine : EngineBase {
                     // products: all heavy items in the kernel with 32-bit
                     // offsets (every entry index < nnz(A) < 2^31)
                     if (da.lean_dense) {
-                        const int dsm = dense_smem(cx);
-                        const int dstat = (int)sizeof(DenseShared<V>) + 256;
-                        const int dper = std::max(1, std::min(2, (227 * 1024) / (dsm + dstat)));
+                        // three CTAs per SM when their shared memory allows it
+                        // (registers are then capped at 40 per thread), else two
+                        const int dsm = heavy32_smem(cx);
+                        const int dstat = (int)sizeof(DenseShared<V>) + 512;
+                        const int dper = std::max(1, std::min(3, (227 * 1024) / (dsm + dstat)));
                         const int dblocks = (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * dper));
                         const int tdd = cx.tbegin(cx.ph_dense, st);
-                        if (dper >= 2)
+                        if (dper >= 3)
+                            k_num_heavy32<I, V, 3><<<dblocks, kDenseChunk, dsm, st>>>(da, c, items, item_order,
+                                                                                     n_items_dev, o.rows, o.vals);
+                        else if (dper == 2)
                             k_num_heavy32<I, V, 2><<<dblocks, kDenseChunk, dsm, st>>>(da, c, items, item_order,
                                                                                      n_items_dev, o.rows, o.vals);
                         else
