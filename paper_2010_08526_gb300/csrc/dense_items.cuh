@@ -94,7 +94,7 @@ __device__ __forceinline__ int warp_offset_total(int n, int *red, int warp, int 
 template <class I, class V, int MINB>
 __global__ void __launch_bounds__(kDenseChunk, MINB)
     k_num_heavy32(GemmArgs<I, V> ga, TierCommon c, const HeavyItem *items, const int32_t *order,
-                  const int64_t *nitems_p, I *out_rows, V *out_vals) {
+                  int64_t nitems, I *out_rows, V *out_vals) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = 1 << c.log2R;
     // dense view: acc[R] + a presence bitmap fb[R/32] (used only when the
@@ -113,7 +113,6 @@ __global__ void __launch_bounds__(kDenseChunk, MINB)
     const int64_t ka = pd->ka, k0 = ga.k0, k1 = ga.k1;
     const int64_t a0 = (int64_t)ap[0];
     const int64_t P1s = (int64_t)c.P + 1;
-    const int64_t nitems = *nitems_p;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const unsigned below_mask = (1u << lane) - 1u;
     const unsigned upto_mask = 0xffffffffu >> (31 - lane);

@@ -393,8 +393,7 @@ template <class I, class V> struct Engine : EngineBase {
                            const int *tc, bool heavy, const int32_t *sym_list,
                            const int32_t *sym_off, const int32_t *heavy_ord,
                            const int32_t *pcnt_in, uint8_t *tier, int32_t *list, int32_t *off,
-                           cudaStream_t st, const HeavyItem *items = nullptr,
-                           const int64_t *n_items_dev = nullptr, int64_t n_items = 0,
+                           cudaStream_t st, const HeavyItem *items = nullptr, int64_t n_items = 0,
                            const int32_t *item_order = nullptr) {
         const int64_t nc = c_hi - c_lo;
         bool any_hash = tc == nullptr;
@@ -450,13 +449,13 @@ template <class I, class V> struct Engine : EngineBase {
                         const int tdd = cx.tbegin(cx.ph_dense, st);
                         if (dper >= 3)
                             k_num_heavy32<I, V, 3><<<dblocks, kDenseChunk, dsm, st>>>(da, c, items, item_order,
-                                                                                     n_items_dev, o.rows, o.vals);
+                                                                                     n_items, o.rows, o.vals);
                         else if (dper == 2)
                             k_num_heavy32<I, V, 2><<<dblocks, kDenseChunk, dsm, st>>>(da, c, items, item_order,
-                                                                                     n_items_dev, o.rows, o.vals);
+                                                                                     n_items, o.rows, o.vals);
                         else
                             k_num_heavy32<I, V, 1><<<dblocks, kDenseChunk, dsm, st>>>(da, c, items, item_order,
-                                                                                     n_items_dev, o.rows, o.vals);
+                                                                                     n_items, o.rows, o.vals);
                         cx.tend(tdd, st);
                         cx.launched();
                         SPG_CK(cudaGetLastError());
@@ -465,10 +464,10 @@ template <class I, class V> struct Engine : EngineBase {
                 }
                 const int td = cx.tbegin(cx.ph_dense, st);
                 if (per_sm == 3)
-                    k_num_heavy<RSrc, HS, 3><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items_dev,
+                    k_num_heavy<RSrc, HS, 3><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items,
                                                                         o.rows, o.vals);
                 else
-                    k_num_heavy<RSrc, HS, 2><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items_dev,
+                    k_num_heavy<RSrc, HS, 2><<<blocks, 512, smem, st>>>(da, c, items, item_order, n_items,
                                                                         o.rows, o.vals);
                 cx.tend(td, st);
                 cx.launched();
@@ -639,9 +638,67 @@ template <class I, class V> struct Engine : EngineBase {
         ps.flops = *(int64_t *)(ps.h_small.as<char>() + 512);
         ps.nnz_c = ps.h_colptr.as<int64_t>()[n];
         SPG_ST(plan_batches(ps));
+        SPG_ST(order_items_by_batch(ps, st));
         if (ps.s > 1) SPG_ST(setup_stage_buffers(ps, st));
         ps.have_symbolic = true;
         return SPGEMM_OK;
+    }
+
+    // Order the heavy items batch-major, panel-major inside a batch, so that a
+    // batch's numeric launch walks its own items only (not every item of the
+    // product with a column-range test); batch_item_off records each batch's
+    // run. The item-count buffer is the scratch: without room for the
+    // (batch, panel) histogram the order is by batch alone, and without room
+    // for that the panel-major order of all items stays.
+    spgemm_status order_items_by_batch(PlanState &ps, cudaStream_t st) {
+        ps.batch_item_off.clear();
+        const int64_t nb = (int64_t)ps.batches.size();
+        if (!ps.nheavy || ps.n_items <= 0 || nb <= 1) return SPGEMM_OK;
+        const int64_t capw = (int64_t)(ps.item_cnt.bytes / sizeof(int64_t));
+        const int64_t caps = (int64_t)(ps.scan_part.bytes / sizeof(int64_t));
+        auto fits = [&](int64_t pe) {
+            const int64_t nbins = nb * pe;
+            return nbins + 1 + nb + 1 <= capw && scan_partials_len(nbins + 1) <= caps;
+        };
+        const int pe = fits(ps.P) ? ps.P : 1;
+        if (!fits(pe)) return SPGEMM_OK;
+        const int64_t nbins = nb * pe;
+        unsigned long long *cnt = ps.item_cnt.as<unsigned long long>();
+        int64_t *bounds = reinterpret_cast<int64_t *>(cnt + nbins + 1);
+        std::vector<int64_t> hb((size_t)nb + 1);
+        for (int64_t t = 0; t < nb; ++t) hb[(size_t)t] = ps.batches[(size_t)t].c0;
+        hb[(size_t)nb] = ps.batches[(size_t)nb - 1].c1;
+        SPG_CK(cudaMemcpyAsync(bounds, hb.data(), sizeof(int64_t) * (size_t)(nb + 1), cudaMemcpyHostToDevice, st));
+        SPG_CK(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (size_t)(nbins + 1), st));
+        const unsigned ob = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ps.n_items + 255) / 256, 4096));
+        const HeavyItem *items = ps.items.as<HeavyItem>();
+        k_items_by_batch<<<ob, 256, 0, st>>>(items, ps.n_items, bounds, nb, pe, 0, cnt, nullptr);
+        SPG_CK(exclusive_scan_i64(reinterpret_cast<int64_t *>(cnt), nbins, reinterpret_cast<int64_t *>(cnt),
+                                  ps.scan_part.as<int64_t>(), 0, st));
+        k_items_by_batch<<<ob, 256, 0, st>>>(items, ps.n_items, bounds, nb, pe, 1, cnt,
+                                             ps.item_order.as<int32_t>());
+        k_batch_item_starts<<<(unsigned)((nb + 1 + 255) / 256), 256, 0, st>>>(cnt, nb, pe, ps.n_items, bounds);
+        ps.timer.launches += 6;
+        SPG_CK(cudaGetLastError());
+        std::vector<int64_t> off((size_t)nb + 1);
+        SPG_CK(cudaMemcpyAsync(off.data(), bounds, sizeof(int64_t) * (size_t)(nb + 1), cudaMemcpyDeviceToHost, st));
+        SPG_CK(cudaStreamSynchronize(st));
+        ps.batch_item_off.swap(off);
+        return SPGEMM_OK;
+    }
+
+    // The heavy items of batch t: its run of item_order when the items are
+    // ordered batch-major, else all of them (the kernels skip other columns).
+    struct BatchItems {
+        int64_t n;
+        const int32_t *order;
+    };
+    static BatchItems batch_items(const PlanState &ps, int64_t t) {
+        if (ps.batch_item_off.size() == ps.batches.size() + 1) {
+            const int64_t a = ps.batch_item_off[(size_t)t];
+            return {ps.batch_item_off[(size_t)t + 1] - a, ps.item_order.as<int32_t>() + a};
+        }
+        return {ps.n_items, ps.item_order.as<int32_t>()};
     }
 
     spgemm_status build_panels(PlanState &ps, cudaStream_t st) {
@@ -917,6 +974,7 @@ template <class I, class V> struct Engine : EngineBase {
     // ---- numeric -------------------------------------------------------------
     spgemm_status numeric(PlanState &ps, int64_t t, spgemm_csc *C, cudaStream_t st) override {
         const Batch &b = ps.batches[(size_t)t];
+        const BatchItems bitems = batch_items(ps, t);
         Ctx cx = make_ctx(ps);
         const int64_t n = ps.n;
         const int64_t *hc = ps.h_colptr.as<int64_t>();
@@ -928,7 +986,7 @@ template <class I, class V> struct Engine : EngineBase {
                 b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                 ps.heavy_ord.as<int32_t>(), ps.pcnt.as<int32_t>(), ps.tier.as<uint8_t>(),
                 ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
-                ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
+                bitems.n, bitems.order)));
         } else if (incremental(ps)) {
             SPG_ST(numeric_incremental(ps, cx, t, C, st));
         } else {
@@ -950,7 +1008,7 @@ template <class I, class V> struct Engine : EngineBase {
                     b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                     ps.heavy_ord.as<int32_t>(), spc, ps.tier.as<uint8_t>(), ps.list_num.as<int32_t>(),
                     ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
-                    ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
+                    bitems.n, bitems.order)));
                 cx.stage_items = false;
             }
             // sort-free hash merge of the stage partials (Sec. IV-D)
@@ -963,7 +1021,7 @@ template <class I, class V> struct Engine : EngineBase {
                 b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                 ps.heavy_ord.as<int32_t>(), ps.pcnt.as<int32_t>(), ps.tier.as<uint8_t>(),
                 ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
-                ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
+                bitems.n, bitems.order)));
         }
         if (ps.opts.sort_output && !ps.defer_sort)
             SPG_ST(sort_batch(cx, ps.colptr.as<int64_t>(), hc[b.c0], b.c0, b.c1, (I *)C->rowidx, (V *)C->vals,
@@ -981,6 +1039,7 @@ template <class I, class V> struct Engine : EngineBase {
     // the final one, with the counts and panel counts of M_t.
     spgemm_status numeric_incremental(PlanState &ps, Ctx &cx, int64_t bi, spgemm_csc *C, cudaStream_t st) {
         const Batch &b = ps.batches[(size_t)bi];
+        const BatchItems bitems = batch_items(ps, bi);
         const int64_t n = ps.n;
         const int64_t *hc = ps.h_colptr.as<int64_t>();
         const int64_t *hs = ps.h_stage_colptr.as<int64_t>();
@@ -1002,8 +1061,7 @@ template <class I, class V> struct Engine : EngineBase {
                 cx, ga, ga, b.c0, b.c1, scnt, ps.cnt.as<int64_t>(), o, b.tc[1 + s].data(), b.heavy > 0,
                 ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(), ps.heavy_ord.as<int32_t>(), spc,
                 ps.tier.as<uint8_t>(), ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st,
-                ps.items.as<HeavyItem>(), ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items,
-                ps.item_order.as<int32_t>())));
+                ps.items.as<HeavyItem>(), bitems.n, bitems.order)));
             if (s == 0) continue;
             // M_s = M_{s-1} + D_s (sort-free hash merge, Sec. IV-D)
             cx.ph_hash = kPhMerge;
@@ -1020,7 +1078,7 @@ template <class I, class V> struct Engine : EngineBase {
                     b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                     ps.heavy_ord.as<int32_t>(), run_pcnt(ps, s), ps.tier.as<uint8_t>(),
                     ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
-                    ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
+                    bitems.n, bitems.order)));
             } else {
                 NumOut<I, V> oc{ps.colptr.as<int64_t>(), hc[b.c0], (I *)C->rowidx, (V *)C->vals};
                 cx.stage_items = false;
@@ -1029,7 +1087,7 @@ template <class I, class V> struct Engine : EngineBase {
                     b.heavy > 0, ps.list_sym.as<int32_t>(), ps.off_sym.as<int32_t>(),
                     ps.heavy_ord.as<int32_t>(), ps.pcnt.as<int32_t>(), ps.tier.as<uint8_t>(),
                     ps.list_num.as<int32_t>(), ps.off_num.as<int32_t>(), st, ps.items.as<HeavyItem>(),
-                    ps.item_off.as<int64_t>() + ps.nheavy, ps.n_items, ps.item_order.as<int32_t>())));
+                    bitems.n, bitems.order)));
             }
         }
         cx.stage_items = false;
@@ -1373,7 +1431,7 @@ template <class I, class V> struct Engine : EngineBase {
             tmp.list_sym.as<int32_t>(), tmp.off_sym.as<int32_t>(), tmp.heavy_ord.as<int32_t>(),
             tmp.pcnt.as<int32_t>(), tmp.tier.as<uint8_t>(), tmp.list_num.as<int32_t>(),
             tmp.off_num.as<int32_t>(), st, tmp.items.as<HeavyItem>(),
-            tmp.item_off.as<int64_t>() + nheavy, n_items, tmp.item_order.as<int32_t>())));
+            n_items, tmp.item_order.as<int32_t>())));
         int errw = 0;
         SPG_CK(cudaMemcpyAsync(&errw, tmp.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         SPG_CK(cudaStreamSynchronize(st));

@@ -1197,6 +1197,14 @@ __global__ void k_heavy_items(const int32_t *list, const int32_t *list_off, cons
 __global__ void k_items_by_panel(const HeavyItem *items, const int64_t *n_items_p, int mode,
                                  int32_t *panel_cnt, int32_t *order);
 __global__ void k_small_excl_scan(int32_t *a, int P);
+// Batch-major item order: key = batch(g) * pe + (pe > 1 ? p0 : 0) over the
+// contiguous column ranges bounds[0..nb] (mode 0: histogram; mode 1: scatter
+// at the scanned offsets), then each batch's first position (defined in
+// util_kernels.cu).
+__global__ void k_items_by_batch(const HeavyItem *items, int64_t n, const int64_t *bounds, int64_t nb,
+                                 int pe, int mode, unsigned long long *cnt, int32_t *order);
+__global__ void k_batch_item_starts(const unsigned long long *cnt, int64_t nb, int pe, int64_t n,
+                                    int64_t *start);
 
 // Range sources: the contributions of column g restricted to panels
 // [p0, p1). seg() yields segments; row(q, tag) is the global row.
@@ -1327,7 +1335,7 @@ template <class I, class V> struct HashSrcOf<SrcPanelRange<I, V>> { using type =
 template <class DSrc, class HSrc, int MINB>
 __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa, TierCommon c,
                                                       const HeavyItem *items, const int32_t *order,
-                                                      const int64_t *nitems_p,
+                                                      int64_t nitems,
                                                       typename DSrc::Idx *out_rows,
                                                       typename DSrc::Val *out_vals) {
     using V = typename DSrc::Val;
@@ -1343,7 +1351,6 @@ __global__ void __launch_bounds__(512, MINB) k_num_heavy(typename DSrc::Args sa,
     for (int r = threadIdx.x; r < R; r += blockDim.x) { acc[r] = V(0); flg[r] = 0; }
     if (threadIdx.x == 0) sh.pos = 0;
     __syncthreads();
-    const int64_t nitems = *nitems_p;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
         const HeavyItem item = items[order[it]];

@@ -205,6 +205,7 @@ struct PlanState {
     DevBuf merge_tmp;
     DevBuf items, item_cnt, item_off, item_order;  // heavy work items (dense panels / hash ranges)
     int64_t n_items = 0;
+    std::vector<int64_t> batch_item_off;   // batch t's items: item_order[off[t], off[t+1])
     HostBuf h_colptr, h_small, h_stage_colptr, h_parts, h_pref_colptr;
     std::vector<DevBuf> ring_col, ring_row, ring_val;   // spgemm_run_batched device ring
     std::vector<DevBuf> ring_pcol, ring_prow, ring_pval;  // pruned copies (opts.prune)

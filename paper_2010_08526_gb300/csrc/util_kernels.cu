@@ -139,6 +139,33 @@ __global__ void k_items_by_panel(const HeavyItem *items, const int64_t *n_items_
     }
 }
 
+__global__ void k_items_by_batch(const HeavyItem *items, int64_t n, const int64_t *bounds, int64_t nb,
+                                 int pe, int mode, unsigned long long *cnt, int32_t *order) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const HeavyItem it = items[i];
+        const int64_t g = it.g;
+        // the batch t with bounds[t] <= g < bounds[t + 1]
+        int64_t lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (bounds[mid] <= g) lo = mid; else hi = mid - 1;
+        }
+        const int64_t key = lo * pe + (pe > 1 ? it.p0 : 0);
+        if (mode == 0) atomicAdd(&cnt[key], 1ull);
+        else order[atomicAdd(&cnt[key], 1ull)] = (int32_t)i;
+    }
+}
+
+// After the scatter cnt[key] is the end of bucket key, so batch t starts at
+// cnt[t * pe - 1] (0 for t = 0) and start[nb] = n.
+__global__ void k_batch_item_starts(const unsigned long long *cnt, int64_t nb, int pe, int64_t n,
+                                    int64_t *start) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > nb) return;
+    start[t] = t == 0 ? 0 : t == nb ? n : (int64_t)cnt[t * pe - 1];
+}
+
 // exclusive scan of P ints in place (one CTA)
 __global__ void k_small_excl_scan(int32_t *a, int P) {
     __shared__ int32_t s[1024];
