@@ -98,9 +98,19 @@ __global__ void __launch_bounds__(kDenseChunk, MINB)
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = 1 << c.log2R;
     // dense view: acc[R] + a presence bitmap fb[R/32] (used only when the
-    // values cannot tell presence); hash view (inside acc): tv[Ti] + tk[Ti]
+    // values cannot tell presence); hash view (inside acc, fixed layout for
+    // every table size Ti <= Tmax): tv[Tmax] values, then tk[Tmax] keys.
+    // Between items the memory is clean for the current view (acc all V(0);
+    // or tv all V(0) and tk all kEmpty), so an item clears nothing: a hash
+    // item resets the slots it filled, a dense item the rows it wrote, and
+    // the key words are rewritten only when the item kind changes (the items
+    // come ordered dense first, then hash, within each batch).
     V *acc = reinterpret_cast<V *>(smem);
     uint32_t *fb = reinterpret_cast<uint32_t *>(smem + sizeof(V) * R);
+    const int Tmax = 2 * c.range_cap;
+    V *tv = reinterpret_cast<V *>(smem);
+    uint32_t *tk = reinterpret_cast<uint32_t *>(smem + sizeof(V) * Tmax);
+    bool hash_view = false;   // the same in every thread
     __shared__ DenseShared<V> sh;
     for (int r = threadIdx.x; r < R; r += blockDim.x) acc[r] = V(0);
     for (int w = threadIdx.x; w < (R >> 5); w += blockDim.x) fb[w] = 0u;
@@ -159,12 +169,22 @@ __global__ void __launch_bounds__(kDenseChunk, MINB)
         const V *cval = ga.apc_val;
         // hash view: the next power of two >= 2 * count slots
         int lt = 6;
-        while ((1 << lt) < 2 * mycnt && (1 << lt) < 2 * c.range_cap) ++lt;
+        while ((1 << lt) < 2 * mycnt && (1 << lt) < Tmax) ++lt;
         const int Ti = 1 << lt;
-        V *tv = reinterpret_cast<V *>(smem);
-        uint32_t *tk = reinterpret_cast<uint32_t *>(smem + sizeof(V) * Ti);
-        if (!dense) {
-            for (int s = threadIdx.x; s < Ti; s += blockDim.x) tk[s] = kEmpty;
+        if (dense == hash_view) {
+            // switch views: the key words become kEmpty (to hash) or V(0)
+            // (to dense); the value words are V(0) in both
+            uint32_t *kw = reinterpret_cast<uint32_t *>(tk);
+            if (dense) {
+                V *a = reinterpret_cast<V *>(kw);
+                const int nv = Tmax * 4 / (int)sizeof(V);
+                for (int r = threadIdx.x; r < nv; r += blockDim.x) a[r] = V(0);
+            } else {
+                uint4 *k4 = reinterpret_cast<uint4 *>(kw);
+                for (int w = threadIdx.x; w < Tmax / 4; w += blockDim.x)
+                    k4[w] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+            }
+            hash_view = !dense;
             __syncthreads();
         }
         // all chunks of the item; mode 0: accumulate the values (dense or
@@ -334,13 +354,11 @@ __global__ void __launch_bounds__(kDenseChunk, MINB)
                         out_rows[out0 + oo] = (I)key;
                         out_vals[out0 + oo] = tv[s];
                     }
+                    tk[s] = kEmpty;
+                    tv[s] = V(0);
                 }
                 o += __popc(bal);
             }
-            __syncthreads();
-            // put back the empty dense view over the bytes the table used
-            const int nacc = min(R, (int)(((int64_t)(sizeof(V) + 4) * Ti + sizeof(V) - 1) / sizeof(V)));
-            for (int r = threadIdx.x; r < nacc; r += blockDim.x) acc[r] = V(0);
             __syncthreads();
             continue;
         }

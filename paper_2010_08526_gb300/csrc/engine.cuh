@@ -438,8 +438,11 @@ template <class I, class V> struct Engine : EngineBase {
                 const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * per_sm));
                 if constexpr (std::is_same<RSrc, SrcPanelRange<I, V>>::value) {
                     // products: all heavy items in the kernel with 32-bit
-                    // offsets (every entry index < nnz(A) < 2^31)
-                    if (da.lean_dense) {
+                    // offsets (every entry index < nnz(A) < 2^31), whose
+                    // largest hash table lies inside the accumulator
+                    const bool table_fits =
+                        2 * range_cap(cx) * (int)(sizeof(V) + 4) <= (1 << cx.tun.log2R) * (int)sizeof(V);
+                    if (da.lean_dense && table_fits) {
                         // three CTAs per SM when their shared memory allows it
                         // (registers are then capped at 40 per thread), else two
                         const int dsm = heavy32_smem(cx);
@@ -644,25 +647,26 @@ template <class I, class V> struct Engine : EngineBase {
         return SPGEMM_OK;
     }
 
-    // Order the heavy items batch-major, panel-major inside a batch, so that a
-    // batch's numeric launch walks its own items only (not every item of the
-    // product with a column-range test); batch_item_off records each batch's
-    // run. The item-count buffer is the scratch: without room for the
-    // (batch, panel) histogram the order is by batch alone, and without room
-    // for that the panel-major order of all items stays.
+    // Order the heavy items batch-major, so that a batch's numeric launch
+    // walks its own items only (not every item of the product with a
+    // column-range test); inside a batch dense items come first, then hash
+    // items, each panel-major. batch_item_off records each batch's run. The
+    // item-count buffer is the scratch: without room for the panel histogram
+    // the order inside a (batch, kind) is arbitrary, and without room for
+    // that the panel-major order of all items stays.
     spgemm_status order_items_by_batch(PlanState &ps, cudaStream_t st) {
         ps.batch_item_off.clear();
         const int64_t nb = (int64_t)ps.batches.size();
-        if (!ps.nheavy || ps.n_items <= 0 || nb <= 1) return SPGEMM_OK;
+        if (!ps.nheavy || ps.n_items <= 0 || nb < 1) return SPGEMM_OK;
         const int64_t capw = (int64_t)(ps.item_cnt.bytes / sizeof(int64_t));
         const int64_t caps = (int64_t)(ps.scan_part.bytes / sizeof(int64_t));
         auto fits = [&](int64_t pe) {
-            const int64_t nbins = nb * pe;
+            const int64_t nbins = nb * 2 * pe;
             return nbins + 1 + nb + 1 <= capw && scan_partials_len(nbins + 1) <= caps;
         };
         const int pe = fits(ps.P) ? ps.P : 1;
         if (!fits(pe)) return SPGEMM_OK;
-        const int64_t nbins = nb * pe;
+        const int64_t nbins = nb * 2 * pe;
         unsigned long long *cnt = ps.item_cnt.as<unsigned long long>();
         int64_t *bounds = reinterpret_cast<int64_t *>(cnt + nbins + 1);
         std::vector<int64_t> hb((size_t)nb + 1);

@@ -1197,10 +1197,10 @@ __global__ void k_heavy_items(const int32_t *list, const int32_t *list_off, cons
 __global__ void k_items_by_panel(const HeavyItem *items, const int64_t *n_items_p, int mode,
                                  int32_t *panel_cnt, int32_t *order);
 __global__ void k_small_excl_scan(int32_t *a, int P);
-// Batch-major item order: key = batch(g) * pe + (pe > 1 ? p0 : 0) over the
-// contiguous column ranges bounds[0..nb] (mode 0: histogram; mode 1: scatter
-// at the scanned offsets), then each batch's first position (defined in
-// util_kernels.cu).
+// Batch-major item order: by batch (the contiguous column ranges
+// bounds[0..nb]), then dense items before hash items, then by first panel
+// when pe > 1 (mode 0: histogram of the keys; mode 1: scatter at the scanned
+// offsets), then each batch's first position (defined in util_kernels.cu).
 __global__ void k_items_by_batch(const HeavyItem *items, int64_t n, const int64_t *bounds, int64_t nb,
                                  int pe, int mode, unsigned long long *cnt, int32_t *order);
 __global__ void k_batch_item_starts(const unsigned long long *cnt, int64_t nb, int pe, int64_t n,

@@ -151,19 +151,21 @@ __global__ void k_items_by_batch(const HeavyItem *items, int64_t n, const int64_
             const int64_t mid = (lo + hi + 1) >> 1;
             if (bounds[mid] <= g) lo = mid; else hi = mid - 1;
         }
-        const int64_t key = lo * pe + (pe > 1 ? it.p0 : 0);
+        // dense items (cnt < 0) before hash items inside a batch
+        const int64_t key = (lo * 2 + (it.cnt < 0 ? 0 : 1)) * pe + (pe > 1 ? it.p0 : 0);
         if (mode == 0) atomicAdd(&cnt[key], 1ull);
         else order[atomicAdd(&cnt[key], 1ull)] = (int32_t)i;
     }
 }
 
-// After the scatter cnt[key] is the end of bucket key, so batch t starts at
-// cnt[t * pe - 1] (0 for t = 0) and start[nb] = n.
+// After the scatter cnt[key] is the end of bucket key; a batch has 2 * pe
+// buckets, so batch t starts at cnt[t * 2 * pe - 1] (0 for t = 0) and
+// start[nb] = n.
 __global__ void k_batch_item_starts(const unsigned long long *cnt, int64_t nb, int pe, int64_t n,
                                     int64_t *start) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t > nb) return;
-    start[t] = t == 0 ? 0 : t == nb ? n : (int64_t)cnt[t * pe - 1];
+    start[t] = t == 0 ? 0 : t == nb ? n : (int64_t)cnt[t * 2 * pe - 1];
 }
 
 // exclusive scan of P ints in place (one CTA)
