@@ -91,10 +91,46 @@ __device__ __forceinline__ int warp_offset_total(int n, int *red, int warp, int 
     return off;
 }
 
+// Inserts a lane's U keys (kEmpty = no key) into a table of 2^log2T slots
+// and returns their slots in slot[u] (-1: no key, or a full table, which sets
+// kErrProbe). Double hashing (an odd step from a second multiplicative hash,
+// so a probe sequence visits every slot) keeps the probe chains short, and a
+// probe is a single compare-and-swap: most keys of a hash-range item are new.
+template <int U>
+__device__ __forceinline__ void hash_insert_dbl(uint32_t *keys, int log2T, const uint32_t (&key)[U],
+                                                int (&slot)[U], int *err) {
+    const uint32_t mask = (1u << log2T) - 1u;
+    uint32_t h[U], step[U];
+    unsigned pending = 0u;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        slot[u] = -1;
+        h[u] = hash_slot(key[u], log2T);
+        step[u] = ((key[u] * 0x85EBCA6Bu) >> (32 - log2T)) | 1u;
+        if (key[u] != kEmpty) pending |= 1u << u;
+    }
+    for (uint32_t probe = 0; pending && probe <= mask; ++probe) {
+        uint32_t cur[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) cur[u] = ((pending >> u) & 1u) ? atomicCAS(&keys[h[u]], kEmpty, key[u]) : 0u;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!((pending >> u) & 1u)) continue;
+            if (cur[u] == kEmpty || cur[u] == key[u]) {
+                slot[u] = (int)h[u];
+                pending &= ~(1u << u);
+            } else {
+                h[u] = (h[u] + step[u]) & mask;
+            }
+        }
+    }
+    if (pending) atomicOr(err, kErrProbe);
+}
+
 template <class I, class V, int MINB>
 __global__ void __launch_bounds__(kDenseChunk, MINB)
     k_num_heavy32(GemmArgs<I, V> ga, TierCommon c, const HeavyItem *items, const int32_t *order,
-                  int64_t nitems, I *out_rows, V *out_vals) {
+                  int64_t nitems, int *next_item, I *out_rows, V *out_vals) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = 1 << c.log2R;
     // dense view: acc[R] + a presence bitmap fb[R/32] (used only when the
@@ -130,7 +166,15 @@ __global__ void __launch_bounds__(kDenseChunk, MINB)
     // (R / nw, a multiple of 32 for R >= 2^10)
     const int rpw = R / nw;
     const int rlo = warp * rpw;
-    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    // items are taken in order from a device counter, one at a time per CTA
+    __shared__ int s_item;
+    auto fetch = [&]() -> int64_t {
+        __syncthreads();   // every thread is past the previous item
+        if (threadIdx.x == 0) s_item = atomicAdd(next_item, 1);
+        __syncthreads();
+        return s_item;
+    };
+    for (int64_t it = fetch(); it < nitems; it = fetch()) {
         const HeavyItem item = items[order[it]];
         const int64_t g = item.g;
         if (g < c.c_lo || g >= c.c_hi) continue;
@@ -322,7 +366,7 @@ __global__ void __launch_bounds__(kDenseChunk, MINB)
                                 }
                             }
                             int hs[kDenseBatch];
-                            hash_insert_all<kDenseBatch>(tk, lt, key, hs, c.err);
+                            hash_insert_dbl<kDenseBatch>(tk, lt, key, hs, c.err);
 #pragma unroll
                             for (int u = 0; u < kDenseBatch; ++u)
                                 if (hs[u] >= 0) atomic_add_v(&tv[hs[u]], x[u]);

@@ -450,15 +450,18 @@ template <class I, class V> struct Engine : EngineBase {
                         const int dper = std::max(1, std::min(3, (227 * 1024) / (dsm + dstat)));
                         const int dblocks = (int)std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)cx.nsm * dper));
                         const int tdd = cx.tbegin(cx.ph_dense, st);
+                        // the item counter (the last int of the binning cursors)
+                        int *next_item = cx.cursor + 63;
+                        SPG_CK(cudaMemsetAsync(next_item, 0, sizeof(int), st));
                         if (dper >= 3)
                             k_num_heavy32<I, V, 3><<<dblocks, kDenseChunk, dsm, st>>>(da, c, items, item_order,
-                                                                                     n_items, o.rows, o.vals);
+                                                                                     n_items, next_item, o.rows, o.vals);
                         else if (dper == 2)
                             k_num_heavy32<I, V, 2><<<dblocks, kDenseChunk, dsm, st>>>(da, c, items, item_order,
-                                                                                     n_items, o.rows, o.vals);
+                                                                                     n_items, next_item, o.rows, o.vals);
                         else
                             k_num_heavy32<I, V, 1><<<dblocks, kDenseChunk, dsm, st>>>(da, c, items, item_order,
-                                                                                     n_items, o.rows, o.vals);
+                                                                                     n_items, next_item, o.rows, o.vals);
                         cx.tend(tdd, st);
                         cx.launched();
                         SPG_CK(cudaGetLastError());
