@@ -233,6 +233,9 @@ template <class I, class V> struct Engine : EngineBase {
         const int per_sm = std::max(1, std::min(2048 / thr, (228 * 1024) / (smem + 34 * 1024)));
         const int want = count < 0 ? cx.nsm * per_sm : count;
         const int blocks = std::max(1, std::min(want, cx.nsm * per_sm));
+        // the tier's column counter: binning cursors 32 + t, zeroed with the
+        // cursors at the start of the pass
+        c.next_col = cx.cursor + 32 + t;
         switch (T) {
             case 512: k_num_block<Src, 512><<<blocks, thr, smem, st>>>(sa, c, rows, vals); break;
             case 1024: k_num_block<Src, 1024><<<blocks, thr, smem, st>>>(sa, c, rows, vals); break;

@@ -65,6 +65,7 @@ template <class I, class V> struct PartDev {
 
 // Arguments shared by all tier kernels (independent of the source).
 struct TierCommon {
+    int *next_col;           // block-tier column counter (zero before the launch)
     const int32_t *list;     // global column ids, grouped by tier
     const int32_t *list_off; // [kTiers+1] tier offsets in list (device)
     int tier;
@@ -616,6 +617,23 @@ __device__ __forceinline__ int hash_insert(uint32_t *keys, int log2T, uint32_t k
     return -1;
 }
 
+// Insert key with double hashing (an odd step from a second multiplicative
+// hash, so the probe sequence visits every slot); each probe is one
+// compare-and-swap, the cheap form when most keys are new. Returns the slot,
+// or -1 (recording kErrProbe) for a full table.
+__device__ __forceinline__ int hash_insert_dbl1(uint32_t *keys, int log2T, uint32_t key, int *err) {
+    const uint32_t mask = (1u << log2T) - 1u;
+    uint32_t h = hash_slot(key, log2T);
+    const uint32_t step = ((key * 0x85EBCA6Bu) >> (32 - log2T)) | 1u;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint32_t cur = atomicCAS(&keys[h], kEmpty, key);
+        if (cur == kEmpty || cur == key) return (int)h;
+        h = (h + step) & mask;
+    }
+    atomicOr(err, kErrProbe);
+    return -1;
+}
+
 // hash_insert for a lane's U keys at once (kEmpty = no key): every round
 // issues the probe loads of all pending keys, then the CAS of those that met
 // an empty slot, then resolves them, so the U probe chains overlap instead of
@@ -1028,10 +1046,24 @@ __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::I
     V *vals = reinterpret_cast<V *>(smem);
     uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * T);
     __shared__ BlockShared<V> sh;
+    __shared__ int s_it;
     if (threadIdx.x == 0) { sh.pos = 0; }
     const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
     const int lane = threadIdx.x & 31;
-    for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {
+    // The table is cleared once; the compaction puts back every slot it
+    // reads occupied, so it is clean again for the next column.
+    auto clear = [&]() {
+        for (int s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = kEmpty; vals[s] = V(0); }
+    };
+    clear();
+    // columns are taken in list order from a device counter, one per CTA at a time
+    auto fetch = [&]() -> int {
+        __syncthreads();
+        if (threadIdx.x == 0) s_it = lo + atomicAdd(c.next_col, 1);
+        __syncthreads();
+        return s_it;
+    };
+    for (int it = fetch(); it < hi; it = fetch()) {
         const int64_t g = c.list[it];
         Src src;
         src.open(sa, g);
@@ -1039,16 +1071,15 @@ __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::I
         const int64_t want = c.colptr[g + 1] - c.colptr[g];
         if (c.hybrid_sort && c.flops && c.flops[g] <= T) {   // the same branch for the whole CTA
             num_block_sorted<Src, T>(src, c, keys, vals, sh, out0, want, out_rows, out_vals);
+            __syncthreads();
+            clear();
             continue;
         }
-        for (int s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = kEmpty; vals[s] = V(0); }
-        __syncthreads();
         auto emit = load_apply(
             [&](int64_t q, V bv, int64_t) { return RowVal<V>{src.row(q), src.val(q, bv)}; },
             [&](const RowVal<V> &e, bool valid) {
                 if (!valid) return;
-                bool nw;
-                const int h = hash_insert(keys, LOG2T, e.r, nw, c.err);
+                const int h = hash_insert_dbl1(keys, LOG2T, e.r, c.err);
                 if (h >= 0) atomic_add_v(&vals[h], e.x);
             });
         block_walk<kWalkBatch>(src, emit, c.short_seg, c.huge_seg, sh);
@@ -1066,6 +1097,8 @@ __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::I
                     out_rows[out0 + r] = (I)key;
                     out_vals[out0 + r] = vals[s];
                 }
+                keys[s] = kEmpty;
+                vals[s] = V(0);
             }
         }
         __syncthreads();
@@ -1073,7 +1106,6 @@ __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::I
             if (sh.pos != want) atomicOr(c.err, kErrCount);
             sh.pos = 0;
         }
-        __syncthreads();
     }
 }
 
