@@ -198,6 +198,7 @@ template <class I, class V> struct Engine : EngineBase {
         const int thr = block_tier_threads(T, cx.tun);
         const int smem = T * 4;
         const int per_sm = std::max(1, std::min(2048 / thr, (228 * 1024) / (smem + 34 * 1024)));
+        c.next_col = cx.cursor + 32 + t;   // zeroed with the cursors at the start of the pass
         const int want = count < 0 ? cx.nsm * per_sm : count;
         const int blocks = std::max(1, std::min(want, cx.nsm * per_sm));
         switch (T) {
@@ -378,6 +379,7 @@ template <class I, class V> struct Engine : EngineBase {
             const int smem = (int)(((cx.Rs + 31) / 32) * 4);
             const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(items, cx.nsm));
             const int tb = cx.tbegin(kPhSymHeavy, st);
+            c.next_col = cx.cursor + 63;   // zeroed with the cursors above
             k_sym_bitmap<Src><<<blocks, 1024, smem, st>>>(sa, c);
             cx.tend(tb, st);
             cx.launched();

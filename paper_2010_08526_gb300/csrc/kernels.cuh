@@ -621,17 +621,26 @@ __device__ __forceinline__ int hash_insert(uint32_t *keys, int log2T, uint32_t k
 // hash, so the probe sequence visits every slot); each probe is one
 // compare-and-swap, the cheap form when most keys are new. Returns the slot,
 // or -1 (recording kErrProbe) for a full table.
-__device__ __forceinline__ int hash_insert_dbl1(uint32_t *keys, int log2T, uint32_t key, int *err) {
+__device__ __forceinline__ int hash_insert_dbl1(uint32_t *keys, int log2T, uint32_t key, int *err,
+                                                bool &is_new) {
     const uint32_t mask = (1u << log2T) - 1u;
     uint32_t h = hash_slot(key, log2T);
     const uint32_t step = ((key * 0x85EBCA6Bu) >> (32 - log2T)) | 1u;
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         const uint32_t cur = atomicCAS(&keys[h], kEmpty, key);
-        if (cur == kEmpty || cur == key) return (int)h;
+        if (cur == kEmpty || cur == key) {
+            is_new = cur == kEmpty;
+            return (int)h;
+        }
         h = (h + step) & mask;
     }
+    is_new = false;
     atomicOr(err, kErrProbe);
     return -1;
+}
+__device__ __forceinline__ int hash_insert_dbl1(uint32_t *keys, int log2T, uint32_t key, int *err) {
+    bool is_new;
+    return hash_insert_dbl1(keys, log2T, key, err, is_new);
 }
 
 // hash_insert for a lane's U keys at once (kEmpty = no key): every round
@@ -799,8 +808,16 @@ __global__ void k_sym_block(typename Src::Args sa, TierCommon c) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *keys = reinterpret_cast<uint32_t *>(smem);
     __shared__ BlockShared<V> sh;
+    __shared__ int s_it;
     const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
-    for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {
+    // columns are taken in list order from a device counter, one per CTA at a time
+    auto fetch = [&]() -> int {
+        __syncthreads();
+        if (threadIdx.x == 0) s_it = lo + atomicAdd(c.next_col, 1);
+        __syncthreads();
+        return s_it;
+    };
+    for (int it = fetch(); it < hi; it = fetch()) {
         const int64_t g = c.list[it];
         Src src;
         src.open(sa, g);
@@ -811,7 +828,7 @@ __global__ void k_sym_block(typename Src::Args sa, TierCommon c) {
                                [&](uint32_t r, bool valid) {
                                    if (!valid) return;
                                    bool nw;
-                                   hash_insert(keys, LOG2T, r, nw, c.err);
+                                   hash_insert_dbl1(keys, LOG2T, r, c.err, nw);
                                    mine += nw;
                                });
         block_walk<kWalkBatch>(src, emit, c.short_seg, c.huge_seg, sh);
@@ -823,7 +840,6 @@ __global__ void k_sym_block(typename Src::Args sa, TierCommon c) {
             v = warp_sum(v);
             if (threadIdx.x == 0) c.cnt[g] = v;
         }
-        __syncthreads();
     }
 }
 
@@ -844,7 +860,15 @@ __global__ void __launch_bounds__(1024, 1) k_sym_bitmap(typename Src::Args sa, T
     const int64_t nitems = (int64_t)(hi - lo) * c.Q;
     const int wordsR = 1 << (c.log2R - 5);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    // items are taken from a device counter, one per CTA at a time
+    __shared__ int s_item;
+    auto fetch = [&]() -> int64_t {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(c.next_col, 1);
+        __syncthreads();
+        return s_item;
+    };
+    for (int64_t item = fetch(); item < nitems; item = fetch()) {
         const int64_t ri = nitems - 1 - item;   // list is ascending in sub-tier
         const int hpos = (int)(ri / c.Q);
         const int q = (int)(ri % c.Q);
