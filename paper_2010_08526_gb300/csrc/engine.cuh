@@ -141,6 +141,7 @@ template <class I, class V> struct Engine : EngineBase {
         set_smem(k_bwd_block<I, V, 8192>, mx);
         set_smem(k_bwd_block<I, V, 16384>, mx);
         set_smem(k_sym_bitmap<SrcGemm<I, V>>, mx);
+        set_smem(k_sym_heavy32<I, V>, mx);
         set_smem(k_sym_bitmap<SrcParts<I, V>>, mx);
         set_smem(k_num_dense<SrcPanel<I, V>>, mx);
         set_smem(k_num_dense<SrcPartsPanel<I, V>>, mx);
@@ -380,7 +381,14 @@ template <class I, class V> struct Engine : EngineBase {
             const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(items, cx.nsm));
             const int tb = cx.tbegin(kPhSymHeavy, st);
             c.next_col = cx.cursor + 63;   // zeroed with the cursors above
-            k_sym_bitmap<Src><<<blocks, 1024, smem, st>>>(sa, c);
+            bool lean = false;
+            if constexpr (std::is_same<Src, SrcGemm<I, V>>::value) {
+                if (sa.lean_sym) {
+                    k_sym_heavy32<I, V><<<blocks, kSymChunk, smem, st>>>(sa, c);
+                    lean = true;
+                }
+            }
+            if (!lean) k_sym_bitmap<Src><<<blocks, 1024, smem, st>>>(sa, c);
             cx.tend(tb, st);
             cx.launched();
         }
@@ -512,6 +520,9 @@ template <class I, class V> struct Engine : EngineBase {
         a.apc_row = ps.apc_row.as<uint32_t>();
         a.apc_val = ps.apc_val.as<V>();
         a.lean_dense = ps.A.nnz < (int64_t(1) << 31) ? 1 : 0;
+        // a chunk's stream is at most kSymChunk columns of A, each of at most
+        // min(m, nnz(A)) entries
+        a.lean_sym = a.lean_dense && std::min<int64_t>(ps.A.nrows, ps.A.nnz) * kSymChunk < (int64_t(1) << 31);
         return a;
     }
 

@@ -102,6 +102,7 @@ template <class I, class V> struct GemmArgs {
     const uint32_t *apc_row;  // global rows
     const V *apc_val;
     int lean_dense;           // heavy items may use 32-bit entry offsets (nnz(A) < 2^31)
+    int lean_sym;             // the heavy symbolic may use 32-bit stream positions too
 };
 
 template <class I, class V> struct PartsArgs {
@@ -1799,4 +1800,5 @@ template <class V> __global__ void k_fill_zero(V *p, int64_t n) {
 }  // namespace spg
 
 #include "dense_items.cuh"
+#include "sym_heavy32.cuh"
 #include "multi_persistent.cuh"
