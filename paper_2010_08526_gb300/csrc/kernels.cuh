@@ -811,10 +811,16 @@ __global__ void k_sym_block(typename Src::Args sa, TierCommon c) {
     __shared__ BlockShared<V> sh;
     __shared__ int s_it;
     const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
-    // columns are taken in list order from a device counter, one per CTA at a time
+    // columns are taken in list order from a device counter, one per CTA at a
+    // time; thread 0 reserves the next one when it starts a column
+    int ahead = 0;
+    if (threadIdx.x == 0) ahead = atomicAdd(c.next_col, 1);
     auto fetch = [&]() -> int {
         __syncthreads();
-        if (threadIdx.x == 0) s_it = lo + atomicAdd(c.next_col, 1);
+        if (threadIdx.x == 0) {
+            s_it = lo + ahead;
+            ahead = atomicAdd(c.next_col, 1);
+        }
         __syncthreads();
         return s_it;
     };
@@ -1081,10 +1087,16 @@ __global__ void k_num_block(typename Src::Args sa, TierCommon c, typename Src::I
         for (int s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = kEmpty; vals[s] = V(0); }
     };
     clear();
-    // columns are taken in list order from a device counter, one per CTA at a time
+    // columns are taken in list order from a device counter, one per CTA at a
+    // time; thread 0 reserves the next one when it starts a column
+    int ahead = 0;
+    if (threadIdx.x == 0) ahead = atomicAdd(c.next_col, 1);
     auto fetch = [&]() -> int {
         __syncthreads();
-        if (threadIdx.x == 0) s_it = lo + atomicAdd(c.next_col, 1);
+        if (threadIdx.x == 0) {
+            s_it = lo + ahead;
+            ahead = atomicAdd(c.next_col, 1);
+        }
         __syncthreads();
         return s_it;
     };

@@ -40,10 +40,17 @@ __global__ void __launch_bounds__(kSymChunk, 1) k_sym_heavy32(GemmArgs<I, V> ga,
     const unsigned below_mask = (1u << lane) - 1u;
     const unsigned upto_mask = 0xffffffffu >> (31 - lane);
     const int64_t k0 = ga.k0, k1 = ga.k1;
+    // items come from a device counter; thread 0 reserves the next item when
+    // it starts one, so the counter's round trip overlaps the item's work
     __shared__ int s_item;
+    int ahead = 0;
+    if (threadIdx.x == 0) ahead = atomicAdd(c.next_col, 1);
     auto fetch = [&]() -> int64_t {
         __syncthreads();
-        if (threadIdx.x == 0) s_item = atomicAdd(c.next_col, 1);
+        if (threadIdx.x == 0) {
+            s_item = ahead;
+            ahead = atomicAdd(c.next_col, 1);
+        }
         __syncthreads();
         return s_item;
     };
