@@ -398,8 +398,8 @@ spgemm_status spgemm_transpose(const spgemm_csc *in, spgemm_csc *out, cudaStream
  * counted, and the largest shared-memory hash table holds 8192 rows; parts
  * that share rows count each copy); larger inputs return SPGEMM_ERR_INVALID
  * with the limit in the message. The first call on each device looks up the
- * array's address on that device, so make it before any stream capture. Every
- * call synchronises the stream once (to read the merged size). All calls on
+ * array's address on that device. Every call synchronises the stream once (to
+ * read the merged size). All calls on
  * one device share that device's array (it keeps the last call's contents):
  * calls that overlap on one GPU race, so serialise them.
  * Errors: as spgemm_merge, plus SPGEMM_ERR_INVALID for sizes beyond the array.

@@ -10,9 +10,8 @@
 // library keeps the array until the process exits.
 //
 // The array's address is looked up once per device (cudaGetSymbolAddress, with
-// that device current) on that device's first call, so that first call should
-// come before any stream capture. Every call synchronises its stream once, to
-// read the merged size. All calls on one device share that device's array and
+// that device current) on that device's first call. Every call synchronises its
+// stream once, to read the merged size. All calls on one device share that device's array and
 // host staging, and the array keeps the last call's contents; the merge clears
 // what it reads before writing. Calls on one device that overlap (other
 // streams, other host threads) race on both and must be serialised by the
