@@ -477,6 +477,33 @@ def test_batches_concatenate_to_unbatched():
     assert_matches(got, ref, ab, nt, label="batched")
 
 
+@pytest.mark.parametrize("nb_target", [1, 2, 20])
+def test_heavy_items_over_many_batches(nb_target):
+    """Heavy columns spread over 1, about 2 and about 20 batches: after the
+    plan the items are ordered batch-major (by batch, kind and panel; by batch
+    and kind when the scratch lacks room for the panel histogram; left in
+    panel order when it lacks room for that), and each batch's launch takes
+    its own run of them. With 24 heavy columns and 6 panels the three cases
+    take the three orders."""
+    A = skewed(6000, 6000, 11, hubs=4, hub_deg=2500, base=6)
+    tun = spg.Tuning(hash_max_cap=256, panel_rows=1024)
+    ref, ab, nt = oracle.spgemm(A, A, with_absterm=True, with_nterm=True)
+    cnt = np.diff(ref.colptr)
+    Ad = to_dev(A)
+    big = 1 << 30
+    probe = spg.Plan(Ad, Ad, budget=big, tuning=tun)
+    cap0 = probe.symbolic()["batch_cap_bytes"]
+    probe.close()
+    r = 12
+    total = r * ref.nnz + 8 * A.ncols
+    target = max(int((r * int(cnt.max()) + 8) * 1.5), total // nb_target + 4096)
+    budget = big - 2 * (cap0 - target)
+    got, info = run(A, A, budget=budget, tuning=tun)
+    assert info["heavy_columns"] > 0
+    assert info["nbatches"] >= (nb_target + 1) // 2, info
+    assert_matches(got, ref, ab, nt, label=f"heavy items, {info['nbatches']} batches")
+
+
 def test_budget_too_small():
     A = W.config1(n=1024)
     with pytest.raises(spg.SpgemmError):
