@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(NT) k_multi_pass(typename Src::Args sa, TierCo
                     [&](const RowVal<V> &e, bool valid) {
                         if (!valid) return;
                         bool nw;
-                        const int h = hash_insert(keys, log2T, e.r, nw, c.err);
+                        const int h = hash_insert_dbl1(keys, log2T, e.r, c.err, nw);
                         if (MODE == 0) mine += nw;
                         else if (h >= 0) atomic_add_v(&vals[h], e.x);
                     });
@@ -204,8 +204,16 @@ __global__ void __launch_bounds__(NT) k_multi_pass(typename Src::Args sa, TierCo
         }
     }
     // warp-sized columns: every warp takes kWarpGrab at a time (one counter
-    // update per grab), each with a warp-private table
+    // update per grab), each with a warp-private table. In the numeric pass the
+    // table is cleared once and the compaction puts back the slots it reads
+    // occupied; the symbolic pass clears it per column.
     constexpr int kWarpGrab = 8;
+    if (MODE == 1) {
+        V *vals = reinterpret_cast<V *>(smem) + warp * TW;
+        uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * NW * TW) + warp * TW;
+        for (int s = lane; s < TW; s += 32) { keys[s] = kEmpty; vals[s] = V(0); }
+        __syncwarp();
+    }
     for (;;) {
         long long wb = 0;
         if (lane == 0) wb = (long long)atomicAdd(mq.counter + 1, (unsigned long long)kWarpGrab);
@@ -223,12 +231,14 @@ __global__ void __launch_bounds__(NT) k_multi_pass(typename Src::Args sa, TierCo
             uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * NW * TW) + warp * TW;
             Src src;
             src.open(sa, g);
-            for (int s = lane; s < T; s += 32) { keys[s] = kEmpty; if (MODE == 1) vals[s] = V(0); }
-            __syncwarp();
+            if (MODE == 0) {
+                for (int s = lane; s < T; s += 32) keys[s] = kEmpty;
+                __syncwarp();
+            }
             int mine = 0;
             auto emit = [&](int64_t q, V bv, int64_t) {
                 bool nw;
-                const int h = hash_insert(keys, log2T, src.row(q), nw, c.err);
+                const int h = hash_insert_dbl1(keys, log2T, src.row(q), c.err, nw);
                 if (MODE == 0) mine += nw;
                 else if (h >= 0) atomic_add_v(&vals[h], src.val(q, bv));
             };
@@ -252,6 +262,8 @@ __global__ void __launch_bounds__(NT) k_multi_pass(typename Src::Args sa, TierCo
                             out_rows[out0 + r] = (I)key;
                             out_vals[out0 + r] = vals[s];
                         }
+                        keys[s] = kEmpty;
+                        vals[s] = V(0);
                     }
                     pos2 += __popc(bal);
                 }
