@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(256) k_sym_warp(typename Src::Args sa, TierCom
         int mine = 0;
         auto emit = [&](int64_t q, V, int64_t) {
             bool nw;
-            hash_insert(keys, LOG2T, src.row(q), nw, c.err);
+            hash_insert_dbl1(keys, LOG2T, src.row(q), c.err, nw);
             mine += nw;
         };
         warp_walk_all(src, emit, c.short_seg);
@@ -938,15 +938,16 @@ __global__ void __launch_bounds__(256) k_num_warp(typename Src::Args sa, TierCom
     uint32_t *keys = reinterpret_cast<uint32_t *>(smem + sizeof(V) * 8 * T) + warp * T;
     const int lo = c.list_off[c.tier], hi = c.list_off[c.tier + 1];
     const int nwarps = gridDim.x * 8;
+    // the table is cleared once; the compaction puts back the slots it reads
+    // occupied, so it is clean again for the warp's next column
+    for (int s = lane; s < T; s += 32) { keys[s] = kEmpty; vals[s] = V(0); }
+    __syncwarp();
     for (int it = lo + blockIdx.x * 8 + warp; it < hi; it += nwarps) {
         const int64_t g = c.list[it];
         Src src;
         src.open(sa, g);
-        for (int s = lane; s < T; s += 32) { keys[s] = kEmpty; vals[s] = V(0); }
-        __syncwarp();
         auto emit = [&](int64_t q, V bv, int64_t) {
-            bool nw;
-            const int h = hash_insert(keys, LOG2T, src.row(q), nw, c.err);
+            const int h = hash_insert_dbl1(keys, LOG2T, src.row(q), c.err);
             if (h >= 0) atomic_add_v(&vals[h], src.val(q, bv));
         };
         warp_walk_all(src, emit, c.short_seg);
@@ -965,6 +966,8 @@ __global__ void __launch_bounds__(256) k_num_warp(typename Src::Args sa, TierCom
                     out_rows[out0 + r] = (I)key;
                     out_vals[out0 + r] = vals[s];
                 }
+                keys[s] = kEmpty;
+                vals[s] = V(0);
             }
             pos += __popc(bal);
         }
