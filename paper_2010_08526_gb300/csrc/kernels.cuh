@@ -592,6 +592,70 @@ __device__ __forceinline__ void warp_walk_all(const Src &src, Emit &emit, int sh
     }
 }
 
+// A value's bits through a warp shuffle (any 4- or 8-byte value type).
+template <class V> __device__ __forceinline__ V shfl_bits(V v, int src) {
+    static_assert(sizeof(V) == 4 || sizeof(V) == 8, "4- or 8-byte values");
+    if constexpr (sizeof(V) == 4) {
+        uint32_t b;
+        memcpy(&b, &v, 4);
+        b = __shfl_sync(SPG_FULL, b, src);
+        memcpy(&v, &b, 4);
+    } else {
+        unsigned long long b;
+        memcpy(&b, &v, 8);
+        b = __shfl_sync(SPG_FULL, b, src);
+        memcpy(&v, &b, 8);
+    }
+    return v;
+}
+
+// Warp-level load-balanced walk over src's segments, for one warp per column:
+// per round of 32 B entries (one per lane) the products form a flattened
+// stream [0, T), walked in 32-wide windows; lane j of a window takes position
+// p, whose segment is the last lane with stream start <= p (a 5-step shuffle
+// search over the lanes' exclusive prefix). load(q, bv) reads entry q (global
+// loads only) and apply(loaded) consumes it; the loads of U windows are
+// issued before the first apply, so a lane keeps U gathers in flight rather
+// than walking its own segment one entry at a time.
+template <int U, class Src, class Load, class Apply>
+__device__ __forceinline__ void warp_walk_flat(const Src &src, Load &load, Apply &apply) {
+    using V = typename Src::Val;
+    using L = decltype(load(int64_t(0), V(0)));
+    const int lane = threadIdx.x & 31;
+    const int64_t nb = src.nseg();
+    for (int64_t base = 0; base < nb; base += 32) {
+        int64_t beg = 0, tag = 0;
+        int len = 0;
+        V bv = V(0);
+        if (base + lane < nb) src.seg(base + lane, beg, len, bv, tag);
+        const int incl = warp_incl_scan(len);
+        const int excl = incl - len;
+        const int T = __shfl_sync(SPG_FULL, incl, 31);
+        for (int w = 0; w < T; w += 32 * U) {
+            L x[U];
+            bool ok[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = w + 32 * u + lane;
+                ok[u] = p < T;
+                int sl = 0;
+#pragma unroll
+                for (int b = 16; b > 0; b >>= 1) {
+                    const int e = __shfl_sync(SPG_FULL, excl, sl + b);
+                    if (e <= p) sl += b;
+                }
+                const int64_t bs = __shfl_sync(SPG_FULL, beg, sl);
+                const int es = __shfl_sync(SPG_FULL, excl, sl);
+                const V vs = shfl_bits(bv, sl);
+                if (ok[u]) x[u] = load(bs + (p - es), vs);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (ok[u]) apply(x[u]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Shared-memory hash tables (linear probing, 32-bit keys)
 // ---------------------------------------------------------------------------

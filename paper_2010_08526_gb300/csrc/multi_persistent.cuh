@@ -236,13 +236,16 @@ __global__ void __launch_bounds__(NT) k_multi_pass(typename Src::Args sa, TierCo
                 __syncwarp();
             }
             int mine = 0;
-            auto emit = [&](int64_t q, V bv, int64_t) {
-                bool nw;
-                const int h = hash_insert_dbl1(keys, log2T, src.row(q), c.err, nw);
-                if (MODE == 0) mine += nw;
-                else if (h >= 0) atomic_add_v(&vals[h], src.val(q, bv));
+            auto ld = [&](int64_t q, V bv) {
+                return RowVal<V>{src.row(q), MODE == 1 ? src.val(q, bv) : V(0)};
             };
-            warp_walk_all(src, emit, c.short_seg);
+            auto ap = [&](const RowVal<V> &e) {
+                bool nw;
+                const int h = hash_insert_dbl1(keys, log2T, e.r, c.err, nw);
+                if (MODE == 0) mine += nw;
+                else if (h >= 0) atomic_add_v(&vals[h], e.x);
+            };
+            warp_walk_flat<4>(src, ld, ap);
             __syncwarp();
             if (MODE == 0) {
                 mine = warp_sum(mine);
