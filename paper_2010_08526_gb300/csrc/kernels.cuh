@@ -854,12 +854,13 @@ __global__ void __launch_bounds__(256) k_sym_warp(typename Src::Args sa, TierCom
         for (int s = lane; s < T; s += 32) keys[s] = kEmpty;
         __syncwarp();
         int mine = 0;
-        auto emit = [&](int64_t q, V, int64_t) {
+        auto ld = [&](int64_t q, V) { return src.row(q); };
+        auto ap = [&](uint32_t r) {
             bool nw;
-            hash_insert_dbl1(keys, LOG2T, src.row(q), c.err, nw);
+            hash_insert_dbl1(keys, LOG2T, r, c.err, nw);
             mine += nw;
         };
-        warp_walk_all(src, emit, c.short_seg);
+        warp_walk_flat<4>(src, ld, ap);
         mine = warp_sum(mine);
         if (lane == 0) c.cnt[g] = mine;
         __syncwarp();
@@ -1010,11 +1011,12 @@ __global__ void __launch_bounds__(256) k_num_warp(typename Src::Args sa, TierCom
         const int64_t g = c.list[it];
         Src src;
         src.open(sa, g);
-        auto emit = [&](int64_t q, V bv, int64_t) {
-            const int h = hash_insert_dbl1(keys, LOG2T, src.row(q), c.err);
-            if (h >= 0) atomic_add_v(&vals[h], src.val(q, bv));
+        auto ld = [&](int64_t q, V bv) { return RowVal<V>{src.row(q), src.val(q, bv)}; };
+        auto ap = [&](const RowVal<V> &e) {
+            const int h = hash_insert_dbl1(keys, LOG2T, e.r, c.err);
+            if (h >= 0) atomic_add_v(&vals[h], e.x);
         };
-        warp_walk_all(src, emit, c.short_seg);
+        warp_walk_flat<4>(src, ld, ap);
         __syncwarp();
         const int64_t out0 = c.colptr[g] - c.out_base;
         const int64_t want = c.colptr[g + 1] - c.colptr[g];
